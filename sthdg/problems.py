@@ -1,0 +1,139 @@
+"""Seeded synthetic space-time problems.
+
+Each function returns a sthdg.assemble.Problem.  Coordinates are (t, x) or
+(t, x, y).  The workloads follow the kinds of test problem of Section 5:
+manufactured smooth solutions for convergence, the rotating Gaussian pulse of
+Section 5.1 on its deforming domain, and the 2D+time rotating / constant flows
+used for solver timing.  No external data is read.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .assemble import Problem
+from .mesh import choose_reflection
+
+PI = np.pi
+
+
+def manufactured_1d(n: int = 32, p: int = 1, nu: float = 1e-4, a: float = 1.0) -> Problem:
+    """1D+time on [0,1]^2, u = sin(2 pi x) exp(-t), constant velocity a."""
+    def u(X):
+        return np.sin(2 * PI * X[..., 1]) * np.exp(-X[..., 0])
+
+    def f(X):
+        t, x = X[..., 0], X[..., 1]
+        e = np.exp(-t)
+        return (-np.sin(2 * PI * x) * e + a * 2 * PI * np.cos(2 * PI * x) * e
+                + nu * 4 * PI * PI * np.sin(2 * PI * x) * e)
+
+    return Problem(D=2, n=n, p=p, nu=nu,
+                   velocity=lambda X: np.full(X.shape[:-1] + (1,), a),
+                   source=f, g_dirichlet=u, u_initial=u, exact=u,
+                   reflect=choose_reflection(2, [a]), name=f"mms1d_n{n}_p{p}")
+
+
+def manufactured_2d(n: int = 48, p: int = 2, nu: float = 1e-6, velocity: str = "rotating",
+                    a_const=(0.7, 0.3)) -> Problem:
+    """2D+time on [0,1]^3, u = sin(pi x) sin(pi y) cos(2 pi t).
+
+    velocity "rotating": a = (-(y - 1/2), x - 1/2); "constant": a = a_const.
+    """
+    def u(X):
+        t, x, y = X[..., 0], X[..., 1], X[..., 2]
+        return np.sin(PI * x) * np.sin(PI * y) * np.cos(2 * PI * t)
+
+    if velocity == "rotating":
+        def vel(X):
+            return np.stack([-(X[..., 2] - 0.5), X[..., 1] - 0.5], axis=-1)
+        amean = [0.0, 0.0]
+    else:
+        ac = np.asarray(a_const, dtype=np.float64)
+
+        def vel(X):
+            return np.broadcast_to(ac, X.shape[:-1] + (2,)).copy()
+        amean = ac
+
+    def f(X):
+        t, x, y = X[..., 0], X[..., 1], X[..., 2]
+        sx, cx = np.sin(PI * x), np.cos(PI * x)
+        sy, cy = np.sin(PI * y), np.cos(PI * y)
+        ct, st = np.cos(2 * PI * t), np.sin(2 * PI * t)
+        a = vel(X)
+        ut = -2 * PI * sx * sy * st
+        ux = PI * cx * sy * ct
+        uy = PI * sx * cy * ct
+        lap = -2 * PI * PI * sx * sy * ct
+        return ut + a[..., 0] * ux + a[..., 1] * uy - nu * lap
+
+    return Problem(D=3, n=n, p=p, nu=nu, velocity=vel, source=f, g_dirichlet=u,
+                   u_initial=u, exact=u, reflect=choose_reflection(3, amean),
+                   name=f"mms2d_{velocity}_n{n}_p{p}")
+
+
+def pure_advection(D: int, n: int, p: int, a=None) -> Problem:
+    """nu = 0, constant velocity, smooth inflow data: the hyperbolic limit.
+
+    With a facet-free mean velocity (choose_reflection) the element graph is
+    acyclic, so the block-scaled trace matrix is unit lower triangular in a
+    topological facet order (Lemma 3.1).
+    """
+    if a is None:
+        a = [0.6] if D == 2 else [0.7, 0.3]
+    a = np.asarray(a, dtype=np.float64)
+
+    def u(X):
+        s = np.zeros(X.shape[:-1])
+        for k in range(1, D):
+            s = s + (X[..., k] - a[k - 1] * X[..., 0])
+        return np.sin(2.0 * s) + 0.5
+
+    return Problem(D=D, n=n, p=p, nu=0.0,
+                   velocity=lambda X: np.broadcast_to(a, X.shape[:-1] + (D - 1,)).copy(),
+                   source=lambda X: np.zeros(X.shape[:-1]), g_dirichlet=u, u_initial=u,
+                   exact=u, reflect=choose_reflection(D, a), name=f"adv{D}d_n{n}_p{p}")
+
+
+def rotating_pulse(n: int, p: int, nu: float, A: float = 0.1) -> Problem:
+    """Rotating Gaussian pulse on a time-dependent domain (Section 5.1).
+
+    a = (-4 x2, 4 x1), f = 0, sigma = 0.1, centre (-0.2, 0.1), T = 1; the
+    uniform mesh of [0,1] x [-1/2,1/2]^2 is deformed by
+    x_i = x_i^u + A (1/2 - x_i^u) sin(2 pi (1/2 - x_i^* + t)), x^* = (x2^u, x1^u).
+    """
+    sig, xc, yc = 0.1, -0.2, 0.1
+
+    def u(X):
+        t, x1, x2 = X[..., 0], X[..., 1], X[..., 2]
+        xt = x1 * np.cos(4 * t) + x2 * np.sin(4 * t)
+        yt = -x1 * np.sin(4 * t) + x2 * np.cos(4 * t)
+        den = 2 * sig ** 2 + 4 * nu * t
+        return sig ** 2 / (sig ** 2 + 2 * nu * t) * np.exp(-((xt - xc) ** 2 + (yt - yc) ** 2) / den)
+
+    def vmap(V):
+        t, xu, yu = V[:, 0].copy(), V[:, 1].copy(), V[:, 2].copy()
+        V[:, 1] = xu + A * (0.5 - xu) * np.sin(2 * PI * (0.5 - yu + t))
+        V[:, 2] = yu + A * (0.5 - yu) * np.sin(2 * PI * (0.5 - xu + t))
+        return V
+
+    return Problem(D=3, n=n, p=p, nu=nu,
+                   velocity=lambda X: np.stack([-4 * X[..., 2], 4 * X[..., 1]], axis=-1),
+                   source=lambda X: np.zeros(X.shape[:-1]), g_dirichlet=u, u_initial=u,
+                   exact=u, reflect=(0, 0, 0), lower=(0.0, -0.5, -0.5), upper=(1.0, 0.5, 0.5),
+                   vertex_map=vmap, name=f"pulse_n{n}_p{p}")
+
+
+def workload(name: str, **kw) -> Problem:
+    """Named synthetic workloads.
+
+    'st1d_n32_p1'  : 1D+time, 32x32 squares x 2 triangles, p=1, a_hat=(1,1), nu=1e-4,
+                     u = sin(2 pi x) e^{-t}  (6,144 unknowns)
+    'st2d_n48_p2'  : 2D+time, 48^3 cubes x 6 tetrahedra, p=2, rotating a, nu=1e-6 (or
+                     nu=1e-2), u = sin(pi x) sin(pi y) cos(2 pi t)  (7,934,976 unknowns)
+    Smaller 2D+time cases of the same family take n and p keywords.
+    """
+    if name == "st1d_n32_p1":
+        return manufactured_1d(n=32, p=1, nu=kw.get("nu", 1e-4))
+    if name == "st2d":
+        return manufactured_2d(n=kw.get("n", 48), p=kw.get("p", 2), nu=kw.get("nu", 1e-6))
+    raise KeyError(name)
