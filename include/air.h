@@ -1,0 +1,158 @@
+/*
+ * air.h -- C ABI of the GB300 AIR-preconditioned GMRES library (libair.so).
+ *
+ * Solves the block-scaled, statically condensed space-time HDG trace system
+ *     A x = b,   A = D_b^{-1} S,  b = D_b^{-1} H
+ * (arXiv:2010.11130, Section 2.5 eq. systemLambda with the facet
+ * block-diagonal left scaling of the Section 4 solver settings) by GMRES
+ * accelerated with l-AIR algebraic multigrid (Section 3).
+ *
+ * Conventions for every entry point:
+ *  - Matrices are CSR: row_ptr int64 [n_rows+1] (row_ptr[0] = 0), col int32
+ *    [nnz] strictly ascending within each row, val float64 [nnz].  Square,
+ *    with a stored nonzero diagonal in every row.
+ *  - Vectors are float64.  "Device" pointers are CUDA global memory of the
+ *    current device; "host" pointers are ordinary (preferably pinned) memory.
+ *  - stream is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  All work is ordered on that stream.
+ *  - The caller owns every pointer it passes.  The library owns the
+ *    hierarchy and its workspace and frees them in air_free.
+ *  - Every function returns a status (AIR_OK = 0, > 0 informational,
+ *    < 0 error).  Nothing throws across the ABI and nothing is printed.
+ */
+#ifndef AIR_H
+#define AIR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+#define AIR_OK                    0
+#define AIR_NOT_CONVERGED         1   /* solve stopped at max_iter; info filled in */
+#define AIR_ERR_INVALID_ARG      -1   /* NULL pointer, bad size or option */
+#define AIR_ERR_CSR_MALFORMED    -2   /* unsorted/out-of-range column, missing or zero
+                                         diagonal, non-finite value, bad row_ptr */
+#define AIR_ERR_OOM              -3   /* device allocation failed */
+#define AIR_ERR_CUDA             -4   /* a CUDA runtime call failed */
+#define AIR_ERR_SINGULAR_COARSE  -5   /* coarsest operator singular to working precision */
+#define AIR_ERR_DEVICE_TIMEOUT   -6   /* a bounded device loop hit its iteration cap */
+#define AIR_ERR_COARSE_TOO_LARGE -7   /* coarsening stalled above max_dense rows */
+#define AIR_ERR_UNSUPPORTED      -8   /* option value not implemented on the GPU path */
+
+/* precision in which the hierarchy is stored and the V-cycle is applied */
+#define AIR_PREC_F64  0
+#define AIR_PREC_F32  1
+
+typedef struct {
+    int64_t n_rows, n_cols, nnz;
+    const int64_t *row_ptr;
+    const int32_t *col;
+    const double *val;
+    int on_device;       /* 1: the three arrays are device pointers, 0: host pointers */
+} air_csr;
+
+typedef struct {
+    double theta;        /* classical strength threshold (Section 4: 0.3 for R, 0.2 for C/F) */
+    int distance;        /* l-AIR neighbourhood distance (Section 4: 1); GPU supports 1 */
+    char relax[16];      /* Jacobi sweep pattern over point sets, e.g. "FCF" */
+    double omega;        /* Jacobi weight */
+    int max_coarse;      /* stop coarsening at or below this many rows */
+    int max_levels;      /* hard cap on levels (<= 32) */
+    int max_dense;       /* largest coarsest level inverted densely */
+    int precision;       /* AIR_PREC_F64 or AIR_PREC_F32 */
+    int restart;         /* GMRES restart length m (<= 32) */
+    int max_iter;        /* total inner GMRES steps */
+    int validate;        /* 1: check the CSR before setup (one extra pass) */
+} air_options;
+
+typedef struct {
+    int iters;           /* total inner GMRES steps */
+    int restarts;        /* completed restart cycles */
+    int vcycles;         /* preconditioner applications */
+    int status;          /* AIR_OK or AIR_NOT_CONVERGED */
+    double relres;       /* final true relative residual ||b - A x|| / ||b|| */
+} air_solve_info;
+
+typedef struct {
+    int64_t n, nnz;      /* rows and stored entries of A_l */
+    int64_t nnz_s;       /* strength graph entries (0 on the coarsest level) */
+    int64_t nc;          /* C points = rows of A_{l+1} (0 on the coarsest level) */
+    int64_t nnz_r;       /* entries of R_l */
+    int64_t n_singular;  /* l-AIR local systems treated as singular (injection rows) */
+    int32_t max_m;       /* largest l-AIR local system */
+    int32_t coarsest;    /* 1 on the last level */
+} air_level_info;
+
+typedef struct air_hierarchy air_hierarchy;   /* opaque, library-owned */
+
+/* Fill *opt with the defaults: theta 0.25, distance 1, relax "FCF", omega 1,
+ * max_coarse 1000, max_levels 25, max_dense 4096, AIR_PREC_F64, restart 30,
+ * max_iter 1000, validate 1. */
+void air_default_options(air_options *opt);
+
+/* Build the l-AIR hierarchy of A (Section 3; Section 4 solver settings):
+ * classical strength of connection, first-pass Ruge-Stueben C/F splitting,
+ * restriction R ~ R_ideal = [-A_cf A_ff^{-1}, I] from one dense local solve
+ * per C point, one-point interpolation P = [W; I], Galerkin A_c = R A P;
+ * repeated until max_coarse, then the coarsest operator is inverted densely.
+ * theta and distance override the fields of opt (opt may be NULL for the
+ * defaults).  If A is on the device and precision is F64, the hierarchy keeps
+ * A's pointers as its finest level: the caller must keep A alive and
+ * unchanged until air_free.  A host A is copied to the device.
+ * Synchronises the stream (level sizes are read back).
+ * Errors: INVALID_ARG, CSR_MALFORMED (validate = 1), OOM, CUDA,
+ * DEVICE_TIMEOUT, COARSE_TOO_LARGE, SINGULAR_COARSE, UNSUPPORTED. */
+int air_setup(const air_csr *A, double theta, int distance, const air_options *opt,
+              void *stream, air_hierarchy **out);
+
+/* One V-cycle x = M^{-1} b (Section 3, x <- x + P (RAP)^{-1} R r, applied
+ * recursively from a zero guess, followed by the relax sweeps).  b and x are
+ * device float64 vectors of length n; an F32 hierarchy converts at the
+ * finest level.  Asynchronous on stream. */
+int air_vcycle(const air_hierarchy *H, const double *b, double *x, void *stream);
+
+/* y = A x for device CSR A and device vectors.  Asynchronous. */
+int air_spmv(const air_csr *A, const double *x, double *y, void *stream);
+
+/* Right-preconditioned flexible GMRES(restart) with classical Gram-Schmidt
+ * applied twice, x0 = 0, until ||b - A x|| / ||b|| <= rtol (the paper's
+ * Krylov method is BiCGSTAB; GMRES is named as an alternative in Section 5.1).
+ * A must be the matrix H was built from.  If A->on_device is 1, b and x are
+ * device vectors; if 0, b and x are host vectors and the library copies b in
+ * and x out (A's values are then taken from the hierarchy's device copy).
+ * Synchronises the stream once per inner step (8-byte residual read).
+ * info may be NULL.  Returns AIR_OK or AIR_NOT_CONVERGED, or an error. */
+int air_gmres_solve(const air_csr *A, const air_hierarchy *H, const double *b, double *x,
+                    double rtol, void *stream, air_solve_info *info);
+
+/* Number of levels of H (>= 1). */
+int air_hierarchy_levels(const air_hierarchy *H);
+
+/* Sizes of level l. */
+int air_hierarchy_info(const air_hierarchy *H, int level, air_level_info *info);
+
+/* Copy one array of level l to host memory dst (caller-sized from
+ * air_hierarchy_info).  what: 0 A.row_ptr (int64 n+1), 1 A.col (int32 nnz),
+ * 2 A.val (float64 nnz), 3 S.row_ptr (int64 n+1), 4 S.col (int32 nnz_s),
+ * 5 cf (int8 n, 1 = C), 6 coarse id (int32 n, -1 for F), 7 R.row_ptr (int64
+ * nc+1), 8 R.col (int32 nnz_r), 9 R.val (float64 nnz_r), 10 P column (int32
+ * n, -1 = empty row; the one-point weight is 1).  Synchronous. */
+int air_hierarchy_export(const air_hierarchy *H, int level, int what, void *dst);
+
+/* Free the hierarchy and its workspace (NULL is a no-op). */
+void air_free(air_hierarchy *H);
+
+/* Number of CUDA kernels this library has launched in the process so far
+ * (diagnostic counter, all threads and devices). */
+unsigned long long air_kernel_launches(void);
+
+/* Static description of a status code. */
+const char *air_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AIR_H */

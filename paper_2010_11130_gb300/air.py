@@ -1,0 +1,250 @@
+"""Thin ctypes binding of libair.so (include/air.h).
+
+Argument marshalling only: every step of setup, V-cycle and GMRES runs in the
+library's CUDA kernels.  torch tensors provide device memory and streams.
+The library must have been built (paper_2010_11130_gb300.build.build());
+loading fails loudly if it is missing -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from .build import LIB
+
+AIR_OK = 0
+AIR_NOT_CONVERGED = 1
+AIR_PREC_F64 = 0
+AIR_PREC_F32 = 1
+
+EXPORTED = ["air_default_options", "air_setup", "air_vcycle", "air_spmv", "air_gmres_solve",
+            "air_hierarchy_levels", "air_hierarchy_info", "air_hierarchy_export", "air_free",
+            "air_status_string", "air_kernel_launches"]
+
+
+class air_csr(C.Structure):
+    _fields_ = [("n_rows", C.c_int64), ("n_cols", C.c_int64), ("nnz", C.c_int64),
+                ("row_ptr", C.c_void_p), ("col", C.c_void_p), ("val", C.c_void_p),
+                ("on_device", C.c_int)]
+
+
+class air_options(C.Structure):
+    _fields_ = [("theta", C.c_double), ("distance", C.c_int), ("relax", C.c_char * 16),
+                ("omega", C.c_double), ("max_coarse", C.c_int), ("max_levels", C.c_int),
+                ("max_dense", C.c_int), ("precision", C.c_int), ("restart", C.c_int),
+                ("max_iter", C.c_int), ("validate", C.c_int)]
+
+
+class air_solve_info(C.Structure):
+    _fields_ = [("iters", C.c_int), ("restarts", C.c_int), ("vcycles", C.c_int),
+                ("status", C.c_int), ("relres", C.c_double)]
+
+
+class air_level_info(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("nnz_s", C.c_int64), ("nc", C.c_int64),
+                ("nnz_r", C.c_int64), ("n_singular", C.c_int64), ("max_m", C.c_int32),
+                ("coarsest", C.c_int32)]
+
+
+class AirError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)} ({status})" if what else status_string(status))
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load libair.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB):
+        raise RuntimeError(f"libair.so not built at {LIB}: run paper_2010_11130_gb300.build.build()")
+    L = C.CDLL(LIB)
+    L.air_default_options.argtypes = [C.POINTER(air_options)]
+    L.air_default_options.restype = None
+    L.air_setup.argtypes = [C.POINTER(air_csr), C.c_double, C.c_int, C.POINTER(air_options), C.c_void_p,
+                            C.POINTER(C.c_void_p)]
+    L.air_setup.restype = C.c_int
+    L.air_vcycle.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    L.air_vcycle.restype = C.c_int
+    L.air_spmv.argtypes = [C.POINTER(air_csr), C.c_void_p, C.c_void_p, C.c_void_p]
+    L.air_spmv.restype = C.c_int
+    L.air_gmres_solve.argtypes = [C.POINTER(air_csr), C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
+                                  C.c_void_p, C.POINTER(air_solve_info)]
+    L.air_gmres_solve.restype = C.c_int
+    L.air_hierarchy_levels.argtypes = [C.c_void_p]
+    L.air_hierarchy_levels.restype = C.c_int
+    L.air_hierarchy_info.argtypes = [C.c_void_p, C.c_int, C.POINTER(air_level_info)]
+    L.air_hierarchy_info.restype = C.c_int
+    L.air_hierarchy_export.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p]
+    L.air_hierarchy_export.restype = C.c_int
+    L.air_free.argtypes = [C.c_void_p]
+    L.air_free.restype = None
+    L.air_kernel_launches.argtypes = []
+    L.air_kernel_launches.restype = C.c_ulonglong
+    L.air_status_string.argtypes = [C.c_int]
+    L.air_status_string.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def status_string(st: int) -> str:
+    return lib().air_status_string(int(st)).decode()
+
+
+def kernel_launches() -> int:
+    """Kernels libair has launched in this process (diagnostic counter)."""
+    return int(lib().air_kernel_launches())
+
+
+def _check(st: int, what: str):
+    if st < 0:
+        raise AirError(st, what)
+    return st
+
+
+def _stream(stream=None) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+@dataclass
+class CSR:
+    """CSR operand; arrays are torch tensors (device) or numpy arrays (host)."""
+    row_ptr: object
+    col: object
+    val: object
+    n: int
+
+    @staticmethod
+    def from_host(row_ptr, col, val, device="cuda"):
+        import torch
+        rp = torch.as_tensor(np.ascontiguousarray(row_ptr, dtype=np.int64)).to(device)
+        ci = torch.as_tensor(np.ascontiguousarray(col, dtype=np.int32)).to(device)
+        v = torch.as_tensor(np.ascontiguousarray(val, dtype=np.float64)).to(device)
+        return CSR(rp, ci, v, len(row_ptr) - 1)
+
+    @property
+    def nnz(self) -> int:
+        return int(self.col.shape[0])
+
+    def c(self) -> air_csr:
+        on_dev = not isinstance(self.val, np.ndarray)
+        ptr = (lambda t: t.data_ptr()) if on_dev else (lambda a: a.ctypes.data)
+        return air_csr(self.n, self.n, self.nnz, ptr(self.row_ptr), ptr(self.col), ptr(self.val),
+                       1 if on_dev else 0)
+
+
+def default_options(**kw) -> air_options:
+    o = air_options()
+    lib().air_default_options(C.byref(o))
+    for k, v in kw.items():
+        if k == "relax":
+            v = v.encode()
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+class Hierarchy:
+    """Library-owned AIR hierarchy (opaque pointer)."""
+
+    _EXPORT = {"A.row_ptr": (0, np.int64), "A.col": (1, np.int32), "A.val": (2, np.float64),
+               "S.row_ptr": (3, np.int64), "S.col": (4, np.int32), "cf": (5, np.int8),
+               "cid": (6, np.int32), "R.row_ptr": (7, np.int64), "R.col": (8, np.int32),
+               "R.val": (9, np.float64), "pcol": (10, np.int32)}
+
+    def __init__(self, handle: int, A: CSR, precision: int):
+        self._h = C.c_void_p(handle)
+        self.A = A                      # keeps an aliased finest matrix alive
+        self.precision = precision
+
+    @property
+    def handle(self):
+        return self._h
+
+    def levels(self) -> int:
+        return lib().air_hierarchy_levels(self._h)
+
+    def info(self, level: int) -> air_level_info:
+        inf = air_level_info()
+        _check(lib().air_hierarchy_info(self._h, level, C.byref(inf)), "air_hierarchy_info")
+        return inf
+
+    def export(self, level: int, what: str) -> np.ndarray:
+        inf = self.info(level)
+        code, dt = self._EXPORT[what]
+        size = {0: inf.n + 1, 1: inf.nnz, 2: inf.nnz, 3: inf.n + 1, 4: inf.nnz_s, 5: inf.n, 6: inf.n,
+                7: inf.nc + 1, 8: inf.nnz_r, 9: inf.nnz_r, 10: inf.n}[code]
+        out = np.empty(size, dtype=dt)
+        if size:
+            _check(lib().air_hierarchy_export(self._h, level, code, out.ctypes.data_as(C.c_void_p)),
+                   f"air_hierarchy_export({what})")
+        return out
+
+    def vcycle(self, b, x=None, stream=None):
+        import torch
+        if x is None:
+            x = torch.empty_like(b)
+        _check(lib().air_vcycle(self._h, C.c_void_p(b.data_ptr()), C.c_void_p(x.data_ptr()),
+                                C.c_void_p(_stream(stream))), "air_vcycle")
+        return x
+
+    def free(self):
+        if self._h is not None and self._h.value:
+            lib().air_free(self._h)
+            self._h = C.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def setup(A: CSR, theta: float = 0.25, distance: int = 1, stream=None, **opts) -> Hierarchy:
+    """air_setup: build the l-AIR hierarchy of A on the GPU."""
+    o = default_options(**opts)
+    h = C.c_void_p(0)
+    Ac = A.c()
+    st = lib().air_setup(C.byref(Ac), float(theta), int(distance), C.byref(o),
+                         C.c_void_p(_stream(stream) if Ac.on_device else 0), C.byref(h))
+    _check(st, "air_setup")
+    return Hierarchy(h.value, A, o.precision)
+
+
+def spmv(A: CSR, x, y=None, stream=None):
+    import torch
+    if y is None:
+        y = torch.empty_like(x)
+    Ac = A.c()
+    _check(lib().air_spmv(C.byref(Ac), C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
+                          C.c_void_p(_stream(stream))), "air_spmv")
+    return y
+
+
+def gmres_solve(A: CSR, H: Hierarchy, b, x=None, rtol: float = 1e-8, stream=None):
+    """air_gmres_solve.  Device tensors for device A; numpy arrays for host A."""
+    Ac = A.c()
+    inf = air_solve_info()
+    if Ac.on_device:
+        import torch
+        if x is None:
+            x = torch.empty_like(b)
+        bp, xp, sp = b.data_ptr(), x.data_ptr(), _stream(stream)
+    else:
+        if x is None:
+            x = np.empty_like(b)
+        bp, xp, sp = b.ctypes.data, x.ctypes.data, 0
+    st = lib().air_gmres_solve(C.byref(Ac), H.handle, C.c_void_p(bp), C.c_void_p(xp), float(rtol),
+                               C.c_void_p(sp), C.byref(inf))
+    _check(st, "air_gmres_solve")
+    return x, inf

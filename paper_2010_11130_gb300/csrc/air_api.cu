@@ -1,0 +1,509 @@
+// C ABI of libair: hierarchy setup (arXiv:2010.11130, Section 3 with the
+// Section 4 solver settings), V-cycle application and flexible GMRES.
+// Host code only orchestrates: every arithmetic step runs in the kernels of
+// setup_kernels.cu, solve_kernels.cu and scan.cu.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <atomic>
+#include <new>
+
+#include "air_internal.cuh"
+
+static std::atomic<unsigned long long> g_launches{0};
+
+unsigned long long air_launch_counter_add(unsigned long long k) { return g_launches.fetch_add(k) + k; }
+
+namespace {
+
+template <typename T>
+int dalloc(T **p, int64_t count) {
+    *p = nullptr;
+    if (count <= 0) count = 1;
+    AIR_CUDA(cudaMalloc((void **)p, (size_t)count * sizeof(T)));
+    return AIR_OK;
+}
+
+template <typename T>
+void dfree(T *&p) {
+    if (p) cudaFree((void *)p);
+    p = nullptr;
+}
+
+int read_i64(const int64_t *d, int64_t *h, cudaStream_t s) {
+    AIR_CUDA(cudaMemcpyAsync(h, d, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    AIR_CUDA(cudaStreamSynchronize(s));
+    return AIR_OK;
+}
+
+int check_err(air_hierarchy *H, cudaStream_t s) {
+    int e = 0;
+    AIR_CUDA(cudaMemcpyAsync(&e, H->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    AIR_CUDA(cudaStreamSynchronize(s));
+    if (e & AIR_DEVERR_CSR) return AIR_ERR_CSR_MALFORMED;
+    if (e & AIR_DEVERR_RS_CAP) return AIR_ERR_DEVICE_TIMEOUT;
+    if (e & AIR_DEVERR_SINGULAR) return AIR_ERR_SINGULAR_COARSE;
+    return AIR_OK;
+}
+
+void free_level(AirLevel &L) {
+    if (L.owns_A) {
+        dfree(L.rp);
+        dfree(L.ci);
+        dfree(L.v);
+    }
+    L.rp = nullptr; L.ci = nullptr; L.v = nullptr;
+    dfree(L.v32); dfree(L.dinv); dfree(L.dinv32);
+    dfree(L.srp); dfree(L.sci);
+    dfree(L.cf); dfree(L.cid); dfree(L.crows);
+    dfree(L.rrp); dfree(L.rci); dfree(L.rv); dfree(L.rv32);
+    dfree(L.pcol);
+    dfree(L.b); dfree(L.x); dfree(L.x2);
+}
+
+void free_workspace(air_hierarchy *H) {
+    dfree(H->V); dfree(H->Z); dfree(H->w); dfree(H->r); dfree(H->partials); dfree(H->hcol);
+    dfree(H->Hm); dfree(H->gvec); dfree(H->cs); dfree(H->sn); dfree(H->y); dfree(H->scal);
+    if (H->h_est) cudaFreeHost(H->h_est);
+    H->h_est = nullptr;
+    H->ws_n = 0;
+    H->ws_m = 0;
+}
+
+// Build level l+1 from level l.  Returns AIR_OK with *stop = 1 when level l
+// is the coarsest.
+int coarsen(air_hierarchy *H, int l, cudaStream_t s, int *stop) {
+    AirLevel &L = H->lev[l];
+    const air_options &o = H->opt;
+    int64_t n = L.n;
+    *stop = 0;
+    // a1 strength
+    int32_t *cnt = nullptr;
+    AIR_TRY(dalloc(&cnt, n + 1));
+    AIR_TRY(dalloc(&L.srp, n + 1));
+    AIR_TRY(air_strength(L, o.theta, nullptr, nullptr, cnt, 0, s));
+    AIR_TRY(air_exclusive_scan_i32(cnt, L.srp, n, s));
+    AIR_TRY(read_i64(L.srp + n, &L.nnz_s, s));
+    AIR_TRY(dalloc(&L.sci, L.nnz_s));
+    AIR_TRY(air_strength(L, o.theta, L.srp, L.sci, nullptr, 1, s));
+    // a2 transpose
+    int64_t *strp = nullptr;
+    int32_t *stci = nullptr, *dmax = nullptr;
+    AIR_TRY(dalloc(&strp, n + 1));
+    AIR_TRY(dalloc(&stci, L.nnz_s));
+    AIR_TRY(air_transpose_pattern(n, L.nnz_s, L.srp, L.sci, strp, stci, cnt, s));
+    // largest |S^T_i| (the transposed counts are still in cnt after the scatter)
+    AIR_TRY(dalloc(&dmax, 1));
+    AIR_CUDA(cudaMemsetAsync(dmax, 0, sizeof(int32_t), s));
+    AIR_TRY(air_reduce_max_i32(cnt, n, dmax, s));
+    int32_t max_st = 0;
+    AIR_CUDA(cudaMemcpyAsync(&max_st, dmax, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    AIR_CUDA(cudaStreamSynchronize(s));
+    // a3 C/F splitting
+    AIR_TRY(dalloc(&L.cf, n));
+    AIR_TRY(air_rs_first_pass(n, L.srp, L.sci, strp, stci, max_st, L.cf, H->d_err, s));
+    AIR_TRY(check_err(H, s));
+    dfree(strp);
+    dfree(stci);
+    int64_t *scanw = nullptr;
+    AIR_TRY(dalloc(&scanw, n + 1));
+    AIR_TRY(dalloc(&L.cid, n));
+    int64_t nc = 0;
+    AIR_TRY(air_coarse_ids(n, L.cf, L.cid, nullptr, scanw, &nc, s));
+    if (nc == 0 || (double)nc > 0.9 * (double)n) {
+        dfree(cnt); dfree(dmax); dfree(scanw);
+        dfree(L.srp); dfree(L.sci); dfree(L.cf); dfree(L.cid);
+        L.nnz_s = 0;
+        *stop = 1;
+        return AIR_OK;
+    }
+    L.nc = nc;
+    AIR_TRY(dalloc(&L.crows, nc));
+    AIR_TRY(air_coarse_ids(n, L.cf, L.cid, L.crows, scanw, &nc, s));
+    // a4 l-AIR restriction
+    AIR_TRY(air_lair_counts(nc, L.crows, L.srp, L.sci, L.cf, cnt, s));
+    AIR_TRY(dalloc(&L.rrp, nc + 1));
+    AIR_TRY(air_exclusive_scan_i32(cnt, L.rrp, nc, s));
+    AIR_CUDA(cudaMemsetAsync(dmax, 0, sizeof(int32_t), s));
+    AIR_TRY(air_reduce_max_i32(cnt, nc, dmax, s));
+    int32_t max_m1 = 0;
+    AIR_CUDA(cudaMemcpyAsync(&max_m1, dmax, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    AIR_TRY(read_i64(L.rrp + nc, &L.nnz_r, s));
+    L.max_m = max_m1 - 1;
+    AIR_TRY(dalloc(&L.rci, L.nnz_r));
+    AIR_TRY(dalloc(&L.rv, L.nnz_r));
+    int64_t *dsing = nullptr;
+    AIR_TRY(dalloc(&dsing, 1));
+    AIR_CUDA(cudaMemsetAsync(dsing, 0, sizeof(int64_t), s));
+    AIR_TRY(air_lair_solve(L, L.max_m, dsing, s));
+    AIR_TRY(read_i64(dsing, &L.n_singular, s));
+    dfree(dsing);
+    // a5 one-point interpolation
+    AIR_TRY(dalloc(&L.pcol, n));
+    AIR_TRY(air_onepoint_P(L, o.theta, s));
+    // a6 Galerkin product
+    AIR_TRY(air_rap_terms(L, cnt, s));
+    AIR_CUDA(cudaMemsetAsync(dmax, 0, sizeof(int32_t), s));
+    AIR_TRY(air_reduce_max_i32(cnt, nc, dmax, s));
+    int32_t max_terms = 0;
+    AIR_CUDA(cudaMemcpyAsync(&max_terms, dmax, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    AIR_CUDA(cudaStreamSynchronize(s));
+    AirLevel &C = H->lev[l + 1];
+    C.n = nc;
+    C.owns_A = 1;
+    int64_t *acrp = nullptr;
+    int32_t *acci = nullptr;
+    double *acv = nullptr;
+    AIR_TRY(air_rap(L, nullptr, nullptr, nullptr, cnt, 0, max_terms, s));
+    AIR_TRY(dalloc(&acrp, nc + 1));
+    AIR_TRY(air_exclusive_scan_i32(cnt, acrp, nc, s));
+    AIR_TRY(read_i64(acrp + nc, &C.nnz, s));
+    AIR_TRY(dalloc(&acci, C.nnz));
+    AIR_TRY(dalloc(&acv, C.nnz));
+    AIR_TRY(air_rap(L, acrp, acci, acv, nullptr, 1, max_terms, s));
+    C.rp = acrp;
+    C.ci = acci;
+    C.v = acv;
+    dfree(cnt); dfree(dmax); dfree(scanw);
+    AIR_CUDA(cudaStreamSynchronize(s));
+    return AIR_OK;
+}
+
+int setup_impl(const air_csr *A, const air_options *opt, cudaStream_t s, air_hierarchy *H) {
+    H->opt = *opt;
+    AIR_CUDA(cudaGetDevice(&H->dev));
+    AIR_TRY(dalloc(&H->d_err, 1));
+    AIR_CUDA(cudaMemsetAsync(H->d_err, 0, sizeof(int), s));
+    AirLevel &L0 = H->lev[0];
+    L0.n = A->n_rows;
+    L0.nnz = A->nnz;
+    if (A->on_device && opt->precision == AIR_PREC_F64) {
+        L0.rp = A->row_ptr; L0.ci = A->col; L0.v = A->val;
+        L0.owns_A = 0;
+    } else {
+        int64_t *rp; int32_t *ci; double *v;
+        AIR_TRY(dalloc(&rp, A->n_rows + 1));
+        AIR_TRY(dalloc(&ci, A->nnz));
+        AIR_TRY(dalloc(&v, A->nnz));
+        L0.rp = rp; L0.ci = ci; L0.v = v;
+        L0.owns_A = 1;
+        cudaMemcpyKind k = A->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        AIR_CUDA(cudaMemcpyAsync(rp, A->row_ptr, (size_t)(A->n_rows + 1) * sizeof(int64_t), k, s));
+        AIR_CUDA(cudaMemcpyAsync(ci, A->col, (size_t)A->nnz * sizeof(int32_t), k, s));
+        AIR_CUDA(cudaMemcpyAsync(v, A->val, (size_t)A->nnz * sizeof(double), k, s));
+    }
+    if (opt->validate) {
+        int64_t last = -1;
+        AIR_TRY(read_i64(L0.rp + L0.n, &last, s));
+        if (last != L0.nnz) return AIR_ERR_CSR_MALFORMED;
+        AIR_TRY(air_validate_csr(L0.n, L0.nnz, L0.rp, L0.ci, L0.v, H->d_err, s));
+        AIR_TRY(check_err(H, s));
+    }
+    int l = 0;
+    for (;;) {
+        H->nlev = l + 1;
+        if (H->lev[l].n <= opt->max_coarse || l == opt->max_levels - 1) break;
+        int stop = 0;
+        AIR_TRY(coarsen(H, l, s, &stop));
+        if (stop) break;
+        ++l;
+    }
+    // coarsest level: dense inverse
+    AirLevel &Lc = H->lev[H->nlev - 1];
+    H->nco = Lc.n;
+    if (Lc.n > opt->max_dense) return AIR_ERR_COARSE_TOO_LARGE;
+    {
+        double *work = nullptr;
+        int64_t n = Lc.n;
+        AIR_TRY(dalloc(&H->cinv, n * n));
+        AIR_CUDA(cudaMallocAsync((void **)&work, (size_t)(2 * n * n + n + 1) * sizeof(double), s));
+        AIR_TRY(air_coarse_inverse(n, Lc.rp, Lc.ci, Lc.v, H->cinv, work, H->d_err, s));
+        cudaFreeAsync(work, s);
+        AIR_TRY(check_err(H, s));
+    }
+    // smoother diagonals, precision copies, V-cycle vectors
+    int f32 = opt->precision == AIR_PREC_F32;
+    for (int q = 0; q < H->nlev; ++q) {
+        AirLevel &L = H->lev[q];
+        if (q + 1 < H->nlev) {
+            AIR_TRY(dalloc(&L.dinv, L.n));
+            if (f32) AIR_TRY(dalloc(&L.dinv32, L.n));
+            AIR_TRY(air_diag_inverse(L.n, L.rp, L.ci, L.v, L.dinv, L.dinv32, s));
+            if (f32) {
+                AIR_TRY(dalloc(&L.v32, L.nnz));
+                AIR_TRY(air_cast_d2f(L.v, L.v32, L.nnz, s));
+                AIR_TRY(dalloc(&L.rv32, L.nnz_r));
+                AIR_TRY(air_cast_d2f(L.rv, L.rv32, L.nnz_r, s));
+            }
+        }
+        size_t es = f32 ? sizeof(float) : sizeof(double);
+        AIR_CUDA(cudaMalloc(&L.b, (size_t)(L.n > 0 ? L.n : 1) * es));
+        AIR_CUDA(cudaMalloc(&L.x, (size_t)(L.n > 0 ? L.n : 1) * es));
+        AIR_CUDA(cudaMalloc(&L.x2, (size_t)(L.n > 0 ? L.n : 1) * es));
+    }
+    if (f32) {
+        AIR_TRY(dalloc(&H->cinv32, H->nco * H->nco));
+        AIR_TRY(air_cast_d2f(H->cinv, H->cinv32, H->nco * H->nco, s));
+    }
+    AIR_CUDA(cudaStreamSynchronize(s));
+    return AIR_OK;
+}
+
+int ensure_workspace(air_hierarchy *H, int64_t n, int m) {
+    if (H->ws_n == n && H->ws_m >= m) return AIR_OK;
+    free_workspace(H);
+    int nblk = air_reduce_nblk(n);
+    AIR_TRY(dalloc(&H->V, (int64_t)(m + 1) * n));
+    AIR_TRY(dalloc(&H->Z, (int64_t)m * n));
+    AIR_TRY(dalloc(&H->partials, (int64_t)(m + 2) * nblk));
+    AIR_TRY(dalloc(&H->hcol, 2 * (m + 2)));
+    AIR_TRY(dalloc(&H->Hm, (int64_t)(m + 1) * m));
+    AIR_TRY(dalloc(&H->gvec, m + 1));
+    AIR_TRY(dalloc(&H->cs, m));
+    AIR_TRY(dalloc(&H->sn, m));
+    AIR_TRY(dalloc(&H->y, m));
+    AIR_TRY(dalloc(&H->scal, 8));
+    AIR_CUDA(cudaMallocHost((void **)&H->h_est, 8 * sizeof(double)));
+    H->ws_n = n;
+    H->ws_m = m;
+    return AIR_OK;
+}
+
+// ||v||^2 into dst (device), via block partials
+int norm2(int64_t n, const double *v, double *partials, int nblk, double *dst, cudaStream_t s) {
+    AIR_TRY(air_dot_partials(n, v, 0, 1, v, partials, nblk, s));
+    AIR_TRY(air_reduce_partials(1, partials, nblk, dst, s));
+    return AIR_OK;
+}
+
+int gmres_impl(const AirLevel &A0, const air_hierarchy *Hc, const double *b, double *x, double rtol,
+               cudaStream_t s, air_solve_info *info) {
+    air_hierarchy *H = const_cast<air_hierarchy *>(Hc);
+    const int64_t n = A0.n;
+    const int m = H->opt.restart;
+    AIR_TRY(ensure_workspace(H, n, m));
+    const int nblk = air_reduce_nblk(n);
+    double *h1 = H->hcol, *h2 = H->hcol + (m + 2);
+    double *sc = H->scal;   // [0] ||b||^2, [1] estimate, [2] h_{j+1,j}, [3] ||r||^2
+    info->iters = 0;
+    info->restarts = 0;
+    info->vcycles = 0;
+    info->relres = 0.0;
+    info->status = AIR_NOT_CONVERGED;
+    AIR_TRY(air_fill_zero(x, n, s));
+    AIR_TRY(norm2(n, b, H->partials, nblk, sc, s));
+    AIR_CUDA(cudaMemcpyAsync(H->h_est, sc, sizeof(double), cudaMemcpyDeviceToHost, s));
+    AIR_CUDA(cudaStreamSynchronize(s));
+    double bnorm = sqrt(H->h_est[0]);
+    if (bnorm == 0.0) {
+        info->status = AIR_OK;
+        return AIR_OK;
+    }
+    int it = 0;
+    for (;;) {
+        // r = b - A x into V_0 and its norm
+        AIR_TRY(air_spmv_f64(n, A0.rp, A0.ci, A0.v, x, H->V, b, s));
+        AIR_TRY(norm2(n, H->V, H->partials, nblk, sc + 3, s));
+        AIR_CUDA(cudaMemcpyAsync(H->h_est + 3, sc + 3, sizeof(double), cudaMemcpyDeviceToHost, s));
+        AIR_CUDA(cudaStreamSynchronize(s));
+        double beta = sqrt(H->h_est[3]);
+        info->relres = beta / bnorm;
+        if (info->relres <= rtol) { info->status = AIR_OK; break; }
+        if (it >= H->opt.max_iter) break;
+        AIR_TRY(air_scale_vec(n, H->V, H->V, sc + 3, 1, s));
+        AIR_CUDA(cudaMemsetAsync(H->gvec, 0, (size_t)(m + 1) * sizeof(double), s));
+        AIR_TRY(air_set_scalar(H->gvec, beta, s));
+        int k = 0;
+        for (int j = 0; j < m && it < H->opt.max_iter; ++j) {
+            double *vj = H->V + (int64_t)j * n, *zj = H->Z + (int64_t)j * n, *w = H->V + (int64_t)(j + 1) * n;
+            AIR_TRY(air_vcycle_run(H, vj, zj, s));
+            info->vcycles++;
+            AIR_TRY(air_spmv_f64(n, A0.rp, A0.ci, A0.v, zj, w, nullptr, s));
+            // classical Gram-Schmidt, twice
+            AIR_TRY(air_dot_partials(n, H->V, n, j + 1, w, H->partials, nblk, s));
+            AIR_TRY(air_reduce_partials(j + 1, H->partials, nblk, h1, s));
+            AIR_TRY(air_update_dot_partials(n, H->V, n, j + 1, h1, w, H->partials, nblk, j + 1, s));
+            AIR_TRY(air_reduce_partials(j + 1, H->partials, nblk, h2, s));
+            AIR_TRY(air_update_dot_partials(n, H->V, n, j + 1, h2, w, H->partials, nblk, -1, s));
+            AIR_TRY(air_reduce_partials(1, H->partials, nblk, sc + 4, s));
+            AIR_TRY(air_arnoldi_givens(j, m, h1, h2, sc + 4, H->Hm, H->cs, H->sn, H->gvec, sc, bnorm, s));
+            AIR_TRY(air_scale_vec(n, w, w, sc + 2, 0, s));
+            AIR_CUDA(cudaMemcpyAsync(H->h_est + 1, sc + 1, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+            AIR_CUDA(cudaStreamSynchronize(s));
+            ++it;
+            k = j + 1;
+            double est = H->h_est[1], hn = H->h_est[2];
+            if (est <= rtol || hn == 0.0 || !(est == est)) break;
+        }
+        AIR_TRY(air_hessenberg_solve(k, m, H->Hm, H->gvec, H->y, s));
+        AIR_TRY(air_axpy_multi(n, H->Z, n, k, H->y, x, s));
+        info->restarts++;
+    }
+    info->iters = it;
+    AIR_CUDA(cudaStreamSynchronize(s));
+    return info->status;
+}
+
+}  // namespace
+
+extern "C" {
+
+void air_default_options(air_options *o) {
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->theta = 0.25;
+    o->distance = 1;
+    strcpy(o->relax, "FCF");
+    o->omega = 1.0;
+    o->max_coarse = 1000;
+    o->max_levels = 25;
+    o->max_dense = 4096;
+    o->precision = AIR_PREC_F64;
+    o->restart = 30;
+    o->max_iter = 1000;
+    o->validate = 1;
+}
+
+int air_setup(const air_csr *A, double theta, int distance, const air_options *opt, void *stream,
+              air_hierarchy **out) {
+    if (!out) return AIR_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!A || !A->row_ptr || !A->col || !A->val || A->n_rows <= 0 || A->n_rows != A->n_cols || A->nnz < A->n_rows ||
+        A->n_rows > INT32_MAX)
+        return AIR_ERR_INVALID_ARG;
+    air_options o;
+    if (opt) o = *opt; else air_default_options(&o);
+    o.theta = theta;
+    o.distance = distance;
+    o.relax[sizeof(o.relax) - 1] = 0;
+    for (const char *c = o.relax; *c; ++c)
+        if (*c != 'F' && *c != 'C') return AIR_ERR_INVALID_ARG;
+    if (!(theta >= 0.0) || !(theta <= 1.0) || o.max_levels < 1 || o.max_levels > AIR_MAX_LEVELS ||
+        o.max_dense < 1 || o.restart < 1 || o.restart > 32 || o.max_iter < 0 ||
+        (o.precision != AIR_PREC_F64 && o.precision != AIR_PREC_F32))
+        return AIR_ERR_INVALID_ARG;
+    if (distance != 1) return AIR_ERR_UNSUPPORTED;
+    air_hierarchy *H = new (std::nothrow) air_hierarchy();
+    if (!H) return AIR_ERR_OOM;
+    int st = setup_impl(A, &o, (cudaStream_t)stream, H);
+    if (st != AIR_OK) {
+        cudaStreamSynchronize((cudaStream_t)stream);
+        air_free(H);
+        return st;
+    }
+    *out = H;
+    return AIR_OK;
+}
+
+int air_vcycle(const air_hierarchy *H, const double *b, double *x, void *stream) {
+    if (!H || !b || !x) return AIR_ERR_INVALID_ARG;
+    return air_vcycle_run(H, b, x, (cudaStream_t)stream);
+}
+
+int air_spmv(const air_csr *A, const double *x, double *y, void *stream) {
+    if (!A || !x || !y || !A->on_device || A->n_rows <= 0) return AIR_ERR_INVALID_ARG;
+    return air_spmv_f64(A->n_rows, A->row_ptr, A->col, A->val, x, y, nullptr, (cudaStream_t)stream);
+}
+
+int air_gmres_solve(const air_csr *A, const air_hierarchy *H, const double *b, double *x, double rtol, void *stream,
+                    air_solve_info *info) {
+    if (!A || !H || !b || !x || !(rtol > 0.0) || A->n_rows != H->lev[0].n) return AIR_ERR_INVALID_ARG;
+    air_solve_info local;
+    if (!info) info = &local;
+    cudaStream_t s = (cudaStream_t)stream;
+    air_hierarchy *Hm = const_cast<air_hierarchy *>(H);
+    int64_t n = A->n_rows;
+    if (A->on_device) {
+        AirLevel A0 = H->lev[0];
+        A0.rp = A->row_ptr; A0.ci = A->col; A0.v = A->val; A0.nnz = A->nnz;
+        return gmres_impl(A0, H, b, x, rtol, s, info);
+    }
+    if (!H->lev[0].owns_A || H->lev[0].v == nullptr) return AIR_ERR_INVALID_ARG;
+    if (!Hm->bd) AIR_TRY(dalloc(&Hm->bd, n));
+    if (!Hm->xd) AIR_TRY(dalloc(&Hm->xd, n));
+    AIR_CUDA(cudaMemcpyAsync(Hm->bd, b, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, s));
+    int st = gmres_impl(H->lev[0], H, Hm->bd, Hm->xd, rtol, s, info);
+    if (st < 0) return st;
+    AIR_CUDA(cudaMemcpyAsync(x, Hm->xd, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    AIR_CUDA(cudaStreamSynchronize(s));
+    return st;
+}
+
+int air_hierarchy_levels(const air_hierarchy *H) { return H ? H->nlev : 0; }
+
+int air_hierarchy_info(const air_hierarchy *H, int level, air_level_info *info) {
+    if (!H || !info || level < 0 || level >= H->nlev) return AIR_ERR_INVALID_ARG;
+    const AirLevel &L = H->lev[level];
+    info->n = L.n;
+    info->nnz = L.nnz;
+    info->nnz_s = L.nnz_s;
+    info->nc = L.nc;
+    info->nnz_r = L.nnz_r;
+    info->n_singular = L.n_singular;
+    info->max_m = L.max_m;
+    info->coarsest = level == H->nlev - 1;
+    return AIR_OK;
+}
+
+int air_hierarchy_export(const air_hierarchy *H, int level, int what, void *dst) {
+    if (!H || !dst || level < 0 || level >= H->nlev) return AIR_ERR_INVALID_ARG;
+    const AirLevel &L = H->lev[level];
+    const void *src = nullptr;
+    size_t bytes = 0;
+    switch (what) {
+    case 0: src = L.rp; bytes = (size_t)(L.n + 1) * 8; break;
+    case 1: src = L.ci; bytes = (size_t)L.nnz * 4; break;
+    case 2: src = L.v; bytes = (size_t)L.nnz * 8; break;
+    case 3: src = L.srp; bytes = (size_t)(L.n + 1) * 8; break;
+    case 4: src = L.sci; bytes = (size_t)L.nnz_s * 4; break;
+    case 5: src = L.cf; bytes = (size_t)L.n; break;
+    case 6: src = L.cid; bytes = (size_t)L.n * 4; break;
+    case 7: src = L.rrp; bytes = (size_t)(L.nc + 1) * 8; break;
+    case 8: src = L.rci; bytes = (size_t)L.nnz_r * 4; break;
+    case 9: src = L.rv; bytes = (size_t)L.nnz_r * 8; break;
+    case 10: src = L.pcol; bytes = (size_t)L.n * 4; break;
+    default: return AIR_ERR_INVALID_ARG;
+    }
+    if (!src) return AIR_ERR_INVALID_ARG;
+    if (bytes == 0) return AIR_OK;
+    AIR_CUDA(cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost));
+    return AIR_OK;
+}
+
+void air_free(air_hierarchy *H) {
+    if (!H) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != H->dev) cudaSetDevice(H->dev);
+    cudaDeviceSynchronize();
+    for (int l = 0; l < AIR_MAX_LEVELS; ++l) free_level(H->lev[l]);
+    dfree(H->cinv);
+    dfree(H->cinv32);
+    dfree(H->d_err);
+    dfree(H->xd);
+    dfree(H->bd);
+    free_workspace(H);
+    if (cur != H->dev) cudaSetDevice(cur);
+    delete H;
+}
+
+unsigned long long air_kernel_launches(void) { return g_launches.load(); }
+
+const char *air_status_string(int s) {
+    switch (s) {
+    case AIR_OK: return "ok";
+    case AIR_NOT_CONVERGED: return "not converged within max_iter";
+    case AIR_ERR_INVALID_ARG: return "invalid argument";
+    case AIR_ERR_CSR_MALFORMED: return "malformed CSR matrix";
+    case AIR_ERR_OOM: return "device out of memory";
+    case AIR_ERR_CUDA: return "CUDA runtime error";
+    case AIR_ERR_SINGULAR_COARSE: return "coarsest operator singular";
+    case AIR_ERR_DEVICE_TIMEOUT: return "device loop hit its iteration cap";
+    case AIR_ERR_COARSE_TOO_LARGE: return "coarsening stalled above max_dense";
+    case AIR_ERR_UNSUPPORTED: return "option not supported on the GPU path";
+    default: return "unknown status";
+    }
+}
+
+}  // extern "C"

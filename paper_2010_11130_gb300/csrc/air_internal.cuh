@@ -1,0 +1,149 @@
+// Internal declarations of libair: device data layout and kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/air.h"
+
+#define AIR_MAX_LEVELS 32
+#define AIR_MAX_RESTART 64
+
+// Return a library status from a CUDA call.
+#define AIR_CUDA(call)                                                        \
+    do {                                                                      \
+        cudaError_t e_ = (call);                                              \
+        if (e_ != cudaSuccess) {                                              \
+            (void)cudaGetLastError();                                         \
+            return e_ == cudaErrorMemoryAllocation ? AIR_ERR_OOM : AIR_ERR_CUDA; \
+        }                                                                     \
+    } while (0)
+
+#define AIR_TRY(expr)                  \
+    do {                               \
+        int s_ = (expr);               \
+        if (s_ != AIR_OK) return s_;   \
+    } while (0)
+
+#define AIR_LAUNCH() AIR_CUDA(cudaGetLastError())
+
+// Every kernel launch passes its grid size through air_counted(), which
+// counts the launch (host-side, for diagnostics) and returns the size.
+unsigned long long air_launch_counter_add(unsigned long long k);
+inline dim3 air_counted(dim3 g) {
+    air_launch_counter_add(1);
+    return g;
+}
+
+// device error flags written by bounded kernels
+#define AIR_DEVERR_RS_CAP 1
+#define AIR_DEVERR_CSR 2
+#define AIR_DEVERR_SINGULAR 4
+
+struct AirLevel {
+    int64_t n = 0, nnz = 0;
+    const int64_t *rp = nullptr;      // A_l (level 0 may alias the caller)
+    const int32_t *ci = nullptr;
+    const double *v = nullptr;
+    int owns_A = 0;
+    float *v32 = nullptr;             // F32 copy of A_l values
+    double *dinv = nullptr;           // 1 / a_ii
+    float *dinv32 = nullptr;
+    // strength graph
+    int64_t nnz_s = 0;
+    int64_t *srp = nullptr;
+    int32_t *sci = nullptr;
+    // splitting
+    int8_t *cf = nullptr;             // 1 = C, 0 = F
+    int32_t *cid = nullptr;           // coarse id or -1
+    int64_t nc = 0;
+    int32_t *crows = nullptr;         // C points ascending (nc)
+    // restriction
+    int64_t nnz_r = 0;
+    int64_t *rrp = nullptr;
+    int32_t *rci = nullptr;
+    double *rv = nullptr;
+    float *rv32 = nullptr;
+    int64_t n_singular = 0;
+    int32_t max_m = 0;
+    // one-point interpolation
+    int32_t *pcol = nullptr;
+    // V-cycle work vectors (precision of the hierarchy)
+    void *b = nullptr, *x = nullptr, *x2 = nullptr;
+};
+
+struct air_hierarchy {
+    int nlev = 0;
+    AirLevel lev[AIR_MAX_LEVELS];
+    air_options opt;
+    int dev = 0;
+    // coarsest: explicit inverse (row major)
+    int64_t nco = 0;
+    double *cinv = nullptr;
+    float *cinv32 = nullptr;
+    // device scalars and scratch
+    int *d_err = nullptr;
+    // GMRES workspace (allocated on first solve)
+    int64_t ws_n = 0;
+    int ws_m = 0;
+    double *V = nullptr, *Z = nullptr, *w = nullptr, *r = nullptr;
+    double *partials = nullptr;       // (m+2) x nblk_reduce
+    double *hcol = nullptr;           // small device arrays for the Arnoldi step
+    double *Hm = nullptr;             // (m+1) x m Hessenberg (column major), rotated
+    double *gvec = nullptr, *cs = nullptr, *sn = nullptr, *y = nullptr;
+    double *scal = nullptr;           // [0] norm, [1] estimate, ...
+    double *h_est = nullptr;          // pinned host mirror of scalars
+    double *xd = nullptr, *bd = nullptr;  // device b and x when the caller passes host vectors
+};
+
+// ------------------------------------------------------------------ launchers
+// scan.cu
+int air_exclusive_scan_i32(const int32_t *in, int64_t *out, int64_t n, cudaStream_t s);
+int air_exclusive_scan_i64(const int64_t *in, int64_t *out, int64_t n, cudaStream_t s);
+int air_reduce_max_i32(const int32_t *in, int64_t n, int32_t *d_out, cudaStream_t s);
+
+// setup_kernels.cu
+int air_validate_csr(int64_t n, int64_t nnz, const int64_t *rp, const int32_t *ci, const double *v,
+                     int *d_err, cudaStream_t s);
+int air_strength(const AirLevel &L, double theta, int64_t *srp, int32_t *sci, int32_t *cnt, int fill,
+                 cudaStream_t s);
+int air_transpose_pattern(int64_t n, int64_t nnz, const int64_t *srp, const int32_t *sci, int64_t *strp,
+                          int32_t *stci, int32_t *work, cudaStream_t s);
+int air_rs_first_pass(int64_t n, const int64_t *srp, const int32_t *sci, const int64_t *strp,
+                      const int32_t *stci, int32_t max_st, int8_t *cf, int *d_err, cudaStream_t s);
+int air_coarse_ids(int64_t n, const int8_t *cf, int32_t *cid, int32_t *crows, int64_t *work, int64_t *nc,
+                   cudaStream_t s);
+int air_lair_counts(int64_t nc, const int32_t *crows, const int64_t *srp, const int32_t *sci, const int8_t *cf,
+                    int32_t *cnt, cudaStream_t s);
+int air_lair_solve(const AirLevel &L, int32_t max_m, int64_t *d_nsing, cudaStream_t s);
+int air_onepoint_P(const AirLevel &L, double theta, cudaStream_t s);
+int air_rap(const AirLevel &L, int64_t *acrp, int32_t *acci, double *acv, int32_t *cnt, int fill,
+            int32_t max_terms, cudaStream_t s);
+int air_rap_terms(const AirLevel &L, int32_t *terms, cudaStream_t s);
+int air_coarse_inverse(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, double *inv,
+                       double *work, int *d_err, cudaStream_t s);
+
+// solve_kernels.cu
+int air_spmv_f64(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, const double *x,
+                 double *y, const double *b, cudaStream_t s);   // y = A x, or y = b - A x if b != NULL
+int air_vcycle_run(const air_hierarchy *H, const double *b, double *x, cudaStream_t s);
+int air_cast_d2f(const double *in, float *out, int64_t n, cudaStream_t s);
+int air_diag_inverse(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, double *dinv,
+                     float *dinv32, cudaStream_t s);
+
+// gmres kernels
+int air_dot_partials(int64_t n, const double *V, int64_t ldv, int k, const double *w, double *partials,
+                     int nblk, cudaStream_t s);
+int air_update_dot_partials(int64_t n, const double *V, int64_t ldv, int k, const double *h, double *w,
+                            double *partials, int nblk, int dots, cudaStream_t s);
+int air_reduce_partials(int k, const double *partials, int nblk, double *out, cudaStream_t s);
+int air_scale_vec(int64_t n, const double *in, double *out, const double *d_norm, int sqrt_of, cudaStream_t s);
+int air_arnoldi_givens(int j, int m, const double *h1, const double *h2, const double *nrm2, double *Hm,
+                       double *cs, double *sn, double *g, double *scal, double bnorm, cudaStream_t s);
+int air_hessenberg_solve(int k, int m, const double *Hm, const double *g, double *y, cudaStream_t s);
+int air_axpy_multi(int64_t n, const double *Z, int64_t ldz, int k, const double *y, double *x, cudaStream_t s);
+int air_fill_zero(double *x, int64_t n, cudaStream_t s);
+int air_set_scalar(double *p, double v, cudaStream_t s);
+int air_norm_init(int64_t n, const double *r, double *partials, int nblk, cudaStream_t s);
+
+int air_reduce_nblk(int64_t n);

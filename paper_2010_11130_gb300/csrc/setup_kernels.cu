@@ -1,0 +1,848 @@
+// Setup-phase kernels of the l-AIR hierarchy (arXiv:2010.11130, Section 3 and
+// the Section 4 solver settings).  Every floating-point step here that decides
+// an integer result or feeds a coarser level is written with explicit
+// round-to-nearest intrinsics (__dmul_rn, __dadd_rn, __dsub_rn, __ddiv_rn) so
+// that no multiply-add is contracted: strength tests, local LU solves and the
+// Galerkin sums reproduce a plain sequential FP64 evaluation bit for bit.
+#include <float.h>
+#include <math.h>
+
+#include "air_internal.cuh"
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ double warp_max_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(FULL, v, o));
+    return v;
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ int64_t global_warp() {
+    return ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+}
+
+__device__ __forceinline__ int64_t warp_count() { return ((int64_t)gridDim.x * blockDim.x) >> 5; }
+
+unsigned grid_for(int64_t work_items, int threads, int64_t cap = 152 * 32) {
+    int64_t b = (work_items + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > cap) b = cap;
+    return (unsigned)b;
+}
+
+// ------------------------------------------------------------- validation
+__global__ void validate_kernel(int64_t n, int64_t nnz, const int64_t *rp, const int32_t *ci,
+                                const double *v, int *err) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t b = rp[i], e = rp[i + 1];
+        bool bad = (i == 0 && b != 0) || b < 0 || e < b || e > nnz;
+        bool diag = false;
+        if (!bad) {
+            int32_t prev = -1;
+            for (int64_t k = b; k < e; ++k) {
+                int32_t c = ci[k];
+                double a = v[k];
+                if (c < 0 || c >= n || c <= prev || !isfinite(a)) { bad = true; break; }
+                if (c == i) diag = (a != 0.0);
+                prev = c;
+            }
+        }
+        if (bad || !diag) atomicOr(err, AIR_DEVERR_CSR);
+    }
+}
+
+// ---------------------------------------------------------------- strength
+// j in S_i iff j != i and |a_ij| >= theta * max_{k != i} |a_ik|; empty if the max is 0.
+template <bool FILL>
+__global__ void strength_kernel(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, double theta,
+                                int32_t *cnt, const int64_t *srp, int32_t *sci) {
+    int lane = threadIdx.x & 31;
+    for (int64_t i = global_warp(); i < n; i += warp_count()) {
+        int64_t b = rp[i], e = rp[i + 1];
+        double m = 0.0;
+        for (int64_t k = b + lane; k < e; k += 32)
+            if (ci[k] != i) m = fmax(m, fabs(v[k]));
+        m = warp_max_d(m);
+        if (m == 0.0) {
+            if (!FILL && lane == 0) cnt[i] = 0;
+            continue;
+        }
+        double thr = __dmul_rn(theta, m);
+        int64_t pos = FILL ? srp[i] : 0;
+        int c = 0;
+        for (int64_t k0 = b; k0 < e; k0 += 32) {
+            int64_t k = k0 + lane;
+            bool s = k < e && ci[k] != i && fabs(v[k]) >= thr;
+            unsigned bal = __ballot_sync(FULL, s);
+            if (FILL && s) sci[pos + __popc(bal & lanemask_lt())] = ci[k];
+            pos += __popc(bal);
+            c += __popc(bal);
+        }
+        if (!FILL && lane == 0) cnt[i] = c;
+    }
+}
+
+// -------------------------------------------------------------- transpose
+__global__ void col_count_kernel(int64_t nnz, const int32_t *sci, int32_t *cnt) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nnz; k += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&cnt[sci[k]], 1);
+}
+
+__global__ void transpose_scatter_kernel(int64_t n, const int64_t *srp, const int32_t *sci, const int64_t *strp,
+                                         int32_t *fill, int32_t *stci) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        for (int64_t k = srp[i]; k < srp[i + 1]; ++k) {
+            int32_t j = sci[k];
+            int32_t p = atomicAdd(&fill[j], 1);
+            stci[strp[j] + p] = (int32_t)i;
+        }
+}
+
+__global__ void sort_rows_kernel(int64_t n, const int64_t *rp, int32_t *ci) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t b = rp[i], e = rp[i + 1];
+        for (int64_t k = b + 1; k < e; ++k) {          // insertion sort (rows are short)
+            int32_t key = ci[k];
+            int64_t t = k - 1;
+            while (t >= b && ci[t] > key) { ci[t + 1] = ci[t]; --t; }
+            ci[t + 1] = key;
+        }
+    }
+}
+
+// ------------------------------------------------- first-pass C/F splitting
+// Sequential Ruge-Stueben first pass (largest measure first, ties to the
+// smallest index) run by ONE thread block.  Undecided points with measure
+// lambda >= 1 live in bucket lambda of a three-level bitmap (64-bit words;
+// level 2 of every bucket is held in shared memory).  Bits are removed
+// lazily: the search validates a candidate (still undecided, measure equal
+// to the bucket) and clears stale bits it meets.  All mutable global state is
+// read with __ldcg (L2) so the single block always sees its own atomics.
+constexpr int8_t ST_F = 0, ST_C = 1, ST_U = 2;
+constexpr int RS_THREADS = 256;
+
+struct RSArgs {
+    int64_t n;
+    const int64_t *srp, *strp;
+    const int32_t *sci, *stci;
+    int32_t *lam;
+    int8_t *state;
+    uint64_t *L0, *L1, *L2;
+    int64_t w0, w1, w2;
+    int nb;            // buckets 0 .. nb-1 (bucket 0 unused)
+    int top;           // largest bucket that may be non-empty
+    int64_t cap;       // bound on search iterations
+    int *err;
+};
+
+__device__ __forceinline__ void rs_insert(const RSArgs &a, uint64_t *L2, int b, int64_t k) {
+    uint64_t m0 = 1ull << (k & 63);
+    uint64_t o0 = atomicOr((unsigned long long *)&a.L0[(int64_t)b * a.w0 + (k >> 6)], (unsigned long long)m0);
+    if (o0 == 0) {
+        int64_t i1 = k >> 6;
+        uint64_t o1 = atomicOr((unsigned long long *)&a.L1[(int64_t)b * a.w1 + (i1 >> 6)],
+                               (unsigned long long)(1ull << (i1 & 63)));
+        if (o1 == 0) {
+            int64_t i2 = i1 >> 6;
+            atomicOr((unsigned long long *)&L2[(int64_t)b * a.w2 + (i2 >> 6)], (unsigned long long)(1ull << (i2 & 63)));
+        }
+    }
+}
+
+__global__ void rs_init_kernel(RSArgs a) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t lam = (int32_t)(a.strp[i + 1] - a.strp[i]);
+        bool isolated = (a.srp[i + 1] == a.srp[i]) && lam == 0;
+        a.lam[i] = lam;
+        a.state[i] = isolated ? ST_F : ST_U;
+        if (!isolated && lam > 0) rs_insert(a, a.L2, lam, i);
+    }
+}
+
+// Warp 0 finds the undecided point of largest measure (ties -> smallest
+// index).  Returns the point, -1 when the largest measure is 0, -2 when the
+// iteration cap is hit.
+__device__ int64_t rs_search(const RSArgs &a, uint64_t *L2s, int *top, int64_t *iters) {
+    int lane = threadIdx.x & 31;
+    int b = *top;
+    while (true) {
+        if (b < 1) { *top = 0; return -1; }
+        if (++(*iters) > a.cap) return -2;
+        int64_t w = -1;
+        for (int64_t base = 0; base < a.w2; base += 32) {
+            uint64_t val = (base + lane < a.w2) ? L2s[(int64_t)b * a.w2 + base + lane] : 0ull;
+            unsigned bal = __ballot_sync(FULL, val != 0ull);
+            if (bal) { w = base + __ffs(bal) - 1; break; }
+        }
+        if (w < 0) { --b; continue; }
+        int64_t res = -3;   // retry
+        if (lane == 0) {
+            uint64_t *p2 = &L2s[(int64_t)b * a.w2 + w];
+            uint64_t l2 = *p2;
+            int bit2 = __ffsll((long long)l2) - 1;
+            int64_t i1 = w * 64 + bit2;
+            uint64_t *p1 = &a.L1[(int64_t)b * a.w1 + i1];
+            uint64_t l1 = __ldcg((const unsigned long long *)p1);
+            if (l1 == 0ull) {
+                *p2 = l2 & ~(1ull << bit2);
+            } else {
+                int bit1 = __ffsll((long long)l1) - 1;
+                int64_t i0 = i1 * 64 + bit1;
+                uint64_t *p0 = &a.L0[(int64_t)b * a.w0 + i0];
+                uint64_t l0 = __ldcg((const unsigned long long *)p0);
+                bool clear0 = false;
+                if (l0 == 0ull) {
+                    clear0 = true;
+                } else {
+                    int bit0 = __ffsll((long long)l0) - 1;
+                    int64_t k = i0 * 64 + bit0;
+                    if (__ldcg(&a.state[k]) == ST_U && __ldcg(&a.lam[k]) == b) {
+                        res = k;
+                    } else {
+                        uint64_t n0 = l0 & ~(1ull << bit0);
+                        *p0 = n0;
+                        clear0 = (n0 == 0ull);
+                    }
+                }
+                if (clear0) {
+                    uint64_t n1 = l1 & ~(1ull << bit1);
+                    *p1 = n1;
+                    if (n1 == 0ull) *p2 = l2 & ~(1ull << bit2);
+                }
+            }
+        }
+        res = __shfl_sync(FULL, res, 0);
+        if (res >= 0) { *top = b; return res; }
+        __syncwarp();
+    }
+}
+
+__global__ void __launch_bounds__(RS_THREADS) rs_main_kernel(RSArgs a) {
+    extern __shared__ uint64_t smem[];
+    uint64_t *L2s = smem;                                  // nb * w2 words
+    int32_t *newF = (int32_t *)(smem + (int64_t)a.nb * a.w2);
+    __shared__ int s_top, s_nf;
+    __shared__ long long s_pick;
+    int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    for (int64_t t = tid; t < (int64_t)a.nb * a.w2; t += blockDim.x) L2s[t] = a.L2[t];
+    if (tid == 0) s_top = a.top;
+    int64_t iters = 0;
+    __syncthreads();
+    for (int64_t pick_no = 0; pick_no <= a.n; ++pick_no) {
+        if (warp == 0) {
+            int top = s_top;
+            int64_t p = rs_search(a, L2s, &top, &iters);
+            if (lane == 0) { s_pick = p; s_top = top; s_nf = 0; if (p >= 0) a.state[p] = ST_C; }
+        }
+        __syncthreads();
+        int64_t i = s_pick;
+        if (i < 0) {
+            if (i == -2 && tid == 0) atomicOr(a.err, AIR_DEVERR_RS_CAP);
+            break;
+        }
+        // undecided strong dependants of i become F
+        for (int64_t q = a.strp[i] + tid; q < a.strp[i + 1]; q += blockDim.x) {
+            int32_t j = a.stci[q];
+            if (__ldcg(&a.state[j]) == ST_U) {
+                a.state[j] = ST_F;
+                newF[atomicAdd(&s_nf, 1)] = j;
+            }
+        }
+        __syncthreads();
+        int nf = s_nf;
+        // measure updates: +1 on S_j of every new F point j, -1 on S_i
+        for (int f = warp; f < nf; f += nwarps) {
+            int32_t j = newF[f];
+            for (int64_t q = a.srp[j] + lane; q < a.srp[j + 1]; q += 32) {
+                int32_t k = a.sci[q];
+                if (__ldcg(&a.state[k]) == ST_U) atomicAdd(&a.lam[k], 1);
+            }
+        }
+        for (int64_t q = a.srp[i] + tid; q < a.srp[i + 1]; q += blockDim.x) {
+            int32_t k = a.sci[q];
+            if (__ldcg(&a.state[k]) == ST_U) atomicSub(&a.lam[k], 1);
+        }
+        __syncthreads();
+        // re-insert every touched undecided point under its new measure
+        for (int f = warp; f < nf; f += nwarps) {
+            int32_t j = newF[f];
+            for (int64_t q = a.srp[j] + lane; q < a.srp[j + 1]; q += 32) {
+                int32_t k = a.sci[q];
+                if (__ldcg(&a.state[k]) == ST_U) {
+                    int32_t l = __ldcg(&a.lam[k]);
+                    if (l > 0) { rs_insert(a, L2s, l, k); atomicMax(&s_top, l); }
+                }
+            }
+        }
+        for (int64_t q = a.srp[i] + tid; q < a.srp[i + 1]; q += blockDim.x) {
+            int32_t k = a.sci[q];
+            if (__ldcg(&a.state[k]) == ST_U) {
+                int32_t l = __ldcg(&a.lam[k]);
+                if (l > 0) { rs_insert(a, L2s, l, k); atomicMax(&s_top, l); }
+            }
+        }
+        __syncthreads();
+    }
+    __syncthreads();
+    for (int64_t k = tid; k < a.n; k += blockDim.x)
+        if (__ldcg(&a.state[k]) == ST_U) a.state[k] = ST_F;
+}
+
+// -------------------------------------------------------------- coarse ids
+__global__ void cflag_kernel(int64_t n, const int8_t *cf, int32_t *flag) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        flag[i] = cf[i] == ST_C ? 1 : 0;
+}
+
+__global__ void cid_kernel(int64_t n, const int8_t *cf, const int64_t *scan, int32_t *cid, int32_t *crows) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (cf[i] == ST_C) {
+            cid[i] = (int32_t)scan[i];
+            crows[scan[i]] = (int32_t)i;
+        } else {
+            cid[i] = -1;
+        }
+    }
+}
+
+// ------------------------------------------------------------ l-AIR solves
+// N_i = S_i intersect F (distance 1), ascending.  Count m_i + 1 entries of R row i.
+__global__ void lair_count_kernel(int64_t nc, const int32_t *crows, const int64_t *srp, const int32_t *sci,
+                                  const int8_t *cf, int32_t *cnt) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nc; t += (int64_t)gridDim.x * blockDim.x) {
+        int32_t i = crows[t];
+        int c = 0;
+        for (int64_t q = srp[i]; q < srp[i + 1]; ++q) c += cf[sci[q]] == ST_F;
+        cnt[t] = c + 1;
+    }
+}
+
+__device__ __forceinline__ int find_sorted(const int32_t *arr, int m, int32_t key) {
+    int lo = 0, hi = m - 1;
+    while (lo <= hi) {
+        int mid = (lo + hi) >> 1;
+        int32_t v = arr[mid];
+        if (v == key) return mid;
+        if (v < key) lo = mid + 1; else hi = mid - 1;
+    }
+    return -1;
+}
+
+// One warp per C point: gather M = A_ff(N_i, N_i)^T and rhs = -A(i, N_i)^T,
+// LU with partial pivoting (ties -> smallest row), forward substitution in
+// ascending and back substitution in descending column order, all with
+// explicitly rounded operations.  |pivot| <= 1e-14 max|M| -> z = 0.
+__global__ void lair_solve_kernel(int64_t nc, const int32_t *crows, const int64_t *rp, const int32_t *ci,
+                                  const double *v, const int64_t *srp, const int32_t *sci, const int8_t *cf,
+                                  const int64_t *rrp, int32_t *rci, double *rv, int maxm, int ld,
+                                  unsigned long long *nsing) {
+    extern __shared__ double lsm[];
+    int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    int64_t per_warp = (int64_t)maxm * ld + maxm + (maxm + 1) / 2 + 1;   // doubles
+    double *M = lsm + wib * per_warp;
+    double *z = M + (int64_t)maxm * ld;
+    int32_t *N = (int32_t *)(z + maxm);
+    for (int64_t t = global_warp(); t < nc; t += warp_count()) {
+        int32_t i = crows[t];
+        // neighbourhood
+        int m = 0;
+        for (int64_t q0 = srp[i]; q0 < srp[i + 1]; q0 += 32) {
+            int64_t q = q0 + lane;
+            int32_t j = q < srp[i + 1] ? sci[q] : -1;
+            bool f = j >= 0 && cf[j] == ST_F;
+            unsigned bal = __ballot_sync(FULL, f);
+            if (f) N[m + __popc(bal & lanemask_lt())] = j;
+            m += __popc(bal);
+        }
+        for (int64_t s = lane; s < (int64_t)m * ld; s += 32) M[s] = 0.0;
+        for (int s = lane; s < m; s += 32) z[s] = 0.0;
+        __syncwarp();
+        double mx = 0.0;
+        for (int b = 0; b < m; ++b) {
+            int32_t r = N[b];
+            for (int64_t q = rp[r] + lane; q < rp[r + 1]; q += 32) {
+                int a = find_sorted(N, m, ci[q]);
+                if (a >= 0) { M[(int64_t)a * ld + b] = v[q]; mx = fmax(mx, fabs(v[q])); }
+            }
+        }
+        for (int64_t q = rp[i] + lane; q < rp[i + 1]; q += 32) {
+            int a = find_sorted(N, m, ci[q]);
+            if (a >= 0) z[a] = -v[q];
+        }
+        mx = warp_max_d(mx);
+        double tol = __dmul_rn(1e-14, mx);
+        __syncwarp();
+        bool singular = false;
+        for (int k = 0; k < m; ++k) {
+            double best = -1.0;
+            int br = m;
+            for (int r = k + lane; r < m; r += 32) {
+                double av = fabs(M[(int64_t)r * ld + k]);
+                if (av > best) { best = av; br = r; }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                double ob = __shfl_xor_sync(FULL, best, o);
+                int orr = __shfl_xor_sync(FULL, br, o);
+                if (ob > best || (ob == best && orr < br)) { best = ob; br = orr; }
+            }
+            if (best <= tol) { singular = true; break; }
+            if (br != k) {
+                for (int c = lane; c < m; c += 32) {
+                    double t1 = M[(int64_t)k * ld + c];
+                    M[(int64_t)k * ld + c] = M[(int64_t)br * ld + c];
+                    M[(int64_t)br * ld + c] = t1;
+                }
+                if (lane == 0) { double t1 = z[k]; z[k] = z[br]; z[br] = t1; }
+            }
+            __syncwarp();
+            double d = M[(int64_t)k * ld + k];
+            for (int r = k + 1 + lane; r < m; r += 32)
+                M[(int64_t)r * ld + k] = __ddiv_rn(M[(int64_t)r * ld + k], d);
+            __syncwarp();
+            int w = m - k - 1;
+            for (int s = lane; s < w * w; s += 32) {
+                int r = k + 1 + s / w, c = k + 1 + s % w;
+                M[(int64_t)r * ld + c] = __dsub_rn(M[(int64_t)r * ld + c],
+                                                   __dmul_rn(M[(int64_t)r * ld + k], M[(int64_t)k * ld + c]));
+            }
+            __syncwarp();
+        }
+        if (singular) {
+            for (int s = lane; s < m; s += 32) z[s] = 0.0;
+            if (lane == 0) atomicAdd(nsing, 1ull);
+        } else {
+            for (int c = 0; c < m; ++c) {
+                __syncwarp();
+                double yc = z[c];
+                for (int r = c + 1 + lane; r < m; r += 32)
+                    z[r] = __dsub_rn(z[r], __dmul_rn(M[(int64_t)r * ld + c], yc));
+            }
+            for (int c = m - 1; c >= 0; --c) {
+                __syncwarp();
+                if (lane == 0) z[c] = __ddiv_rn(z[c], M[(int64_t)c * ld + c]);
+                __syncwarp();
+                double xc = z[c];
+                for (int r = lane; r < c; r += 32)
+                    z[r] = __dsub_rn(z[r], __dmul_rn(M[(int64_t)r * ld + c], xc));
+            }
+        }
+        __syncwarp();
+        // R row: N_i with z, plus i with 1, ascending
+        int64_t pos = rrp[t];
+        int before = 0;
+        for (int a0 = 0; a0 < m; a0 += 32) {
+            int a = a0 + lane;
+            bool lt = a < m && N[a] < i;
+            before += __popc(__ballot_sync(FULL, lt));
+            if (a < m) {
+                int64_t p = pos + a + (N[a] > i ? 1 : 0);
+                rci[p] = N[a];
+                rv[p] = z[a];
+            }
+        }
+        if (lane == 0) { rci[pos + before] = i; rv[pos + before] = 1.0; }
+        __syncwarp();
+    }
+}
+
+// --------------------------------------------------------- one-point P
+// F point i: strong C neighbour of largest |a_ij| (ties -> smallest j), weight 1;
+// none -> -1.  C point: its own coarse id.
+__global__ void onepoint_kernel(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, double theta,
+                                const int8_t *cf, const int32_t *cid, int32_t *pcol) {
+    int lane = threadIdx.x & 31;
+    for (int64_t i = global_warp(); i < n; i += warp_count()) {
+        if (cf[i] == ST_C) {
+            if (lane == 0) pcol[i] = cid[i];
+            continue;
+        }
+        int64_t b = rp[i], e = rp[i + 1];
+        double m = 0.0;
+        for (int64_t k = b + lane; k < e; k += 32)
+            if (ci[k] != i) m = fmax(m, fabs(v[k]));
+        m = warp_max_d(m);
+        int32_t best = INT32_MAX;
+        double bv = -1.0;
+        if (m > 0.0) {
+            double thr = __dmul_rn(theta, m);
+            for (int64_t k = b + lane; k < e; k += 32) {
+                int32_t c = ci[k];
+                double a = fabs(v[k]);
+                if (c != i && a >= thr && cf[c] == ST_C && a > bv) { bv = a; best = c; }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            double ob = __shfl_xor_sync(FULL, bv, o);
+            int32_t oc = __shfl_xor_sync(FULL, best, o);
+            if (ob > bv || (ob == bv && oc < best)) { bv = ob; best = oc; }
+        }
+        if (lane == 0) pcol[i] = (best != INT32_MAX) ? cid[best] : -1;
+    }
+}
+
+// ---------------------------------------------------------------- RAP
+__global__ void rap_terms_kernel(int64_t nc, const int64_t *rrp, const int32_t *rci, const int64_t *rp,
+                                 int32_t *terms) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nc; t += (int64_t)gridDim.x * blockDim.x) {
+        int64_t s = 0;
+        for (int64_t q = rrp[t]; q < rrp[t + 1]; ++q) s += rp[rci[q] + 1] - rp[rci[q]];
+        terms[t] = (int32_t)(s < INT32_MAX ? s : INT32_MAX);
+    }
+}
+
+// One warp per coarse row i.  Stage 1: (RA)_ij over R entries k ascending and
+// A row k, accumulated into a per-warp shared hash table (within one k the
+// columns j are distinct, so no two lanes touch one slot).  Stage 2: keys
+// (P(j), j) sorted by a bitonic network, then every coarse column sums its
+// terms in ascending j.  COUNT mode only counts the coarse columns.
+template <bool FILL>
+__global__ void rap_kernel(int64_t nc, const int64_t *rrp, const int32_t *rci, const double *rv,
+                           const int64_t *rp, const int32_t *ci, const double *v, const int32_t *pcol,
+                           int hs_bits, int32_t *cnt, const int64_t *acrp, int32_t *acci, double *acv) {
+    extern __shared__ unsigned char rsm[];
+    const int HS = 1 << hs_bits, HH = HS >> 1;
+    int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    unsigned char *base = rsm + (size_t)wib * (size_t)HS * 20;
+    double *vals = (double *)base;                          // HS
+    unsigned long long *skey = (unsigned long long *)(vals + HS);   // HH
+    double *sval = (double *)(skey + HH);                   // HH
+    int32_t *keys = (int32_t *)(sval + HH);                 // HS
+    for (int64_t t = global_warp(); t < nc; t += warp_count()) {
+        for (int s = lane; s < HS; s += 32) keys[s] = -1;
+        __syncwarp();
+        for (int64_t q = rrp[t]; q < rrp[t + 1]; ++q) {
+            int32_t k = rci[q];
+            double rik = FILL ? rv[q] : 0.0;
+            for (int64_t e = rp[k] + lane; e < rp[k + 1]; e += 32) {
+                int32_t j = ci[e];
+                unsigned h = ((unsigned)j * 2654435761u) >> (32 - hs_bits);
+                while (true) {
+                    int32_t old = atomicCAS(&keys[h], -1, j);
+                    if (old == -1) { if (FILL) vals[h] = 0.0; break; }
+                    if (old == j) break;
+                    h = (h + 1) & (HS - 1);
+                }
+                if (FILL) vals[h] = __dadd_rn(vals[h], __dmul_rn(rik, v[e]));
+            }
+            __syncwarp();
+        }
+        int cntv = 0;
+        for (int s0 = 0; s0 < HS; s0 += 32) {
+            int s = s0 + lane;
+            int32_t j = keys[s];
+            int32_t J = j >= 0 ? pcol[j] : -1;
+            bool ok = J >= 0;
+            unsigned bal = __ballot_sync(FULL, ok);
+            if (ok) {
+                int p = cntv + __popc(bal & lanemask_lt());
+                skey[p] = ((unsigned long long)(unsigned)J << 32) | (unsigned)j;
+                if (FILL) sval[p] = vals[s];
+            }
+            cntv += __popc(bal);
+        }
+        int P = 1;
+        while (P < cntv) P <<= 1;
+        for (int s = cntv + lane; s < P; s += 32) skey[s] = ~0ull;
+        __syncwarp();
+        for (int size = 2; size <= P; size <<= 1) {
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int idx = lane; idx < (P >> 1); idx += 32) {
+                    int a = 2 * stride * (idx / stride) + (idx % stride);
+                    int b = a + stride;
+                    bool up = (a & size) == 0;
+                    unsigned long long ka = skey[a], kb = skey[b];
+                    if ((ka > kb) == up) {
+                        skey[a] = kb; skey[b] = ka;
+                        if (FILL) { double t1 = sval[a]; sval[a] = sval[b]; sval[b] = t1; }
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        int heads = 0;
+        int64_t out = FILL ? acrp[t] : 0;
+        for (int s0 = 0; s0 < cntv; s0 += 32) {
+            int s = s0 + lane;
+            bool head = s < cntv && (s == 0 || (skey[s] >> 32) != (skey[s - 1] >> 32));
+            unsigned bal = __ballot_sync(FULL, head);
+            if (FILL && head) {
+                unsigned long long J = skey[s] >> 32;
+                double acc = 0.0;
+                for (int u = s; u < cntv && (skey[u] >> 32) == J; ++u) acc = __dadd_rn(acc, sval[u]);
+                int64_t p = out + heads + __popc(bal & lanemask_lt());
+                acci[p] = (int32_t)J;
+                acv[p] = acc;
+            }
+            heads += __popc(bal);
+        }
+        if (!FILL && lane == 0) cnt[t] = heads;
+        __syncwarp();
+    }
+}
+
+// ------------------------------------------------------- coarsest inverse
+// Gauss-Jordan with partial pivoting (ties -> smallest row) on [A | I],
+// one pivot step per pair of launches.
+__global__ void dense_scatter_kernel(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
+                                     double *M) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        for (int64_t k = rp[i]; k < rp[i + 1]; ++k) M[i * 2 * n + ci[k]] = v[k];
+        M[i * 2 * n + n + i] = 1.0;
+    }
+}
+
+__global__ void dense_absmax_kernel(int64_t n, const double *M, double *out) {
+    __shared__ double red[32];
+    double m = 0.0;
+    for (int64_t s = threadIdx.x; s < n * n; s += blockDim.x) m = fmax(m, fabs(M[(s / n) * 2 * n + s % n]));
+    m = warp_max_d(m);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        t = warp_max_d(t);
+        if (threadIdx.x == 0) *out = t;
+    }
+}
+
+__global__ void gj_pivot_kernel(int64_t n, int64_t k, double *M, double *fcol, const double *amax, int *err) {
+    __shared__ double sb[32];
+    __shared__ int64_t sr[32];
+    __shared__ int64_t piv;
+    int tid = threadIdx.x;
+    double best = -1.0;
+    int64_t br = n;
+    for (int64_t r = k + tid; r < n; r += blockDim.x) {
+        double a = fabs(M[r * 2 * n + k]);
+        if (a > best) { best = a; br = r; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        double ob = __shfl_xor_sync(FULL, best, o);
+        int64_t orr = __shfl_xor_sync(FULL, br, o);
+        if (ob > best || (ob == best && orr < br)) { best = ob; br = orr; }
+    }
+    if ((tid & 31) == 0) { sb[tid >> 5] = best; sr[tid >> 5] = br; }
+    __syncthreads();
+    if (tid == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+            if (sb[w] > sb[0] || (sb[w] == sb[0] && sr[w] < sr[0])) { sb[0] = sb[w]; sr[0] = sr[w]; }
+        piv = sr[0];
+        if (!(sb[0] > 1e-14 * amax[0])) { atomicOr(err, AIR_DEVERR_SINGULAR); piv = -1; }
+    }
+    __syncthreads();
+    int64_t p = piv;
+    if (p < 0) return;
+    if (p != k)
+        for (int64_t c = k + tid; c < 2 * n; c += blockDim.x) {
+            double t1 = M[k * 2 * n + c];
+            M[k * 2 * n + c] = M[p * 2 * n + c];
+            M[p * 2 * n + c] = t1;
+        }
+    __syncthreads();
+    double d = M[k * 2 * n + k];
+    __syncthreads();
+    for (int64_t c = k + tid; c < 2 * n; c += blockDim.x) M[k * 2 * n + c] = M[k * 2 * n + c] / d;
+    for (int64_t r = tid; r < n; r += blockDim.x) fcol[r] = (r == k) ? 0.0 : M[r * 2 * n + k];
+}
+
+__global__ void gj_eliminate_kernel(int64_t n, int64_t k, double *M, const double *fcol, const int *err) {
+    if (*err & AIR_DEVERR_SINGULAR) return;
+    int64_t w = 2 * n - k;
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n * w; s += (int64_t)gridDim.x * blockDim.x) {
+        int64_t r = s / w, c = k + s % w;
+        double f = fcol[r];
+        if (r != k && f != 0.0) M[r * 2 * n + c] -= f * M[k * 2 * n + c];
+    }
+}
+
+__global__ void dense_extract_kernel(int64_t n, const double *M, double *inv) {
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n * n; s += (int64_t)gridDim.x * blockDim.x)
+        inv[s] = M[(s / n) * 2 * n + n + s % n];
+}
+
+}  // namespace
+
+// ================================================================ launchers
+int air_validate_csr(int64_t n, int64_t nnz, const int64_t *rp, const int32_t *ci, const double *v, int *d_err,
+                     cudaStream_t s) {
+    validate_kernel<<<air_counted(grid_for(n, 256)), 256, 0, s>>>(n, nnz, rp, ci, v, d_err);
+    AIR_LAUNCH();
+    return AIR_OK;
+}
+
+int air_strength(const AirLevel &L, double theta, int64_t *srp, int32_t *sci, int32_t *cnt, int fill,
+                 cudaStream_t s) {
+    unsigned g = grid_for(L.n * 32, 256);
+    if (fill)
+        strength_kernel<true><<<air_counted(g), 256, 0, s>>>(L.n, L.rp, L.ci, L.v, theta, nullptr, srp, sci);
+    else
+        strength_kernel<false><<<air_counted(g), 256, 0, s>>>(L.n, L.rp, L.ci, L.v, theta, cnt, nullptr, nullptr);
+    AIR_LAUNCH();
+    return AIR_OK;
+}
+
+// work: int32 [n] scratch.  strp gets the transposed row pointer.
+int air_transpose_pattern(int64_t n, int64_t nnz, const int64_t *srp, const int32_t *sci, int64_t *strp,
+                          int32_t *stci, int32_t *work, cudaStream_t s) {
+    AIR_CUDA(cudaMemsetAsync(work, 0, (size_t)n * sizeof(int32_t), s));
+    if (nnz > 0) col_count_kernel<<<air_counted(grid_for(nnz, 256)), 256, 0, s>>>(nnz, sci, work);
+    AIR_LAUNCH();
+    AIR_TRY(air_exclusive_scan_i32(work, strp, n, s));
+    AIR_CUDA(cudaMemsetAsync(work, 0, (size_t)n * sizeof(int32_t), s));
+    transpose_scatter_kernel<<<air_counted(grid_for(n, 256)), 256, 0, s>>>(n, srp, sci, strp, work, stci);
+    sort_rows_kernel<<<air_counted(grid_for(n, 256)), 256, 0, s>>>(n, strp, stci);
+    AIR_LAUNCH();
+    return AIR_OK;
+}
+
+int air_rs_first_pass(int64_t n, const int64_t *srp, const int32_t *sci, const int64_t *strp, const int32_t *stci,
+                      int32_t max_st, int8_t *cf, int *d_err, cudaStream_t s) {
+    RSArgs a;
+    a.n = n; a.srp = srp; a.sci = sci; a.strp = strp; a.stci = stci;
+    a.state = cf;
+    a.nb = 2 * max_st + 1;
+    if (a.nb < 2) a.nb = 2;
+    a.top = a.nb - 1;
+    a.w0 = (n + 63) / 64;
+    a.w1 = (a.w0 + 63) / 64;
+    a.w2 = (a.w1 + 63) / 64;
+    a.err = d_err;
+    int64_t nnz_s = 0;
+    AIR_CUDA(cudaMemcpyAsync(&nnz_s, srp + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    AIR_CUDA(cudaStreamSynchronize(s));
+    a.cap = 16 * (n + nnz_s) + 4096;
+    size_t words = (size_t)a.nb * (size_t)(a.w0 + a.w1 + a.w2);
+    uint64_t *bits = nullptr;
+    int32_t *lam = nullptr;
+    AIR_CUDA(cudaMallocAsync(&bits, words * sizeof(uint64_t), s));
+    AIR_CUDA(cudaMallocAsync(&lam, (size_t)n * sizeof(int32_t), s));
+    AIR_CUDA(cudaMemsetAsync(bits, 0, words * sizeof(uint64_t), s));
+    a.L0 = bits;
+    a.L1 = bits + (size_t)a.nb * a.w0;
+    a.L2 = a.L1 + (size_t)a.nb * a.w1;
+    a.lam = lam;
+    rs_init_kernel<<<air_counted(grid_for(n, 256)), 256, 0, s>>>(a);
+    AIR_LAUNCH();
+    size_t smem = (size_t)a.nb * a.w2 * sizeof(uint64_t) + (size_t)(max_st + 1) * sizeof(int32_t);
+    AIR_CUDA(cudaFuncSetAttribute(rs_main_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    rs_main_kernel<<<air_counted(1), RS_THREADS, smem, s>>>(a);
+    AIR_LAUNCH();
+    cudaFreeAsync(bits, s);
+    cudaFreeAsync(lam, s);
+    return AIR_OK;
+}
+
+// work: int64 [n+1]
+int air_coarse_ids(int64_t n, const int8_t *cf, int32_t *cid, int32_t *crows, int64_t *work, int64_t *nc,
+                   cudaStream_t s) {
+    int32_t *flag = nullptr;
+    AIR_CUDA(cudaMallocAsync(&flag, (size_t)(n > 0 ? n : 1) * sizeof(int32_t), s));
+    cflag_kernel<<<air_counted(grid_for(n, 256)), 256, 0, s>>>(n, cf, flag);
+    AIR_LAUNCH();
+    AIR_TRY(air_exclusive_scan_i32(flag, work, n, s));
+    AIR_CUDA(cudaMemcpyAsync(nc, work + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    if (crows) {
+        cid_kernel<<<air_counted(grid_for(n, 256)), 256, 0, s>>>(n, cf, work, cid, crows);
+        AIR_LAUNCH();
+    }
+    cudaFreeAsync(flag, s);
+    AIR_CUDA(cudaStreamSynchronize(s));
+    return AIR_OK;
+}
+
+int air_lair_counts(int64_t nc, const int32_t *crows, const int64_t *srp, const int32_t *sci, const int8_t *cf,
+                    int32_t *cnt, cudaStream_t s) {
+    lair_count_kernel<<<air_counted(grid_for(nc, 256)), 256, 0, s>>>(nc, crows, srp, sci, cf, cnt);
+    AIR_LAUNCH();
+    return AIR_OK;
+}
+
+int air_lair_solve(const AirLevel &L, int32_t max_m, int64_t *d_nsing, cudaStream_t s) {
+    int maxm = max_m < 1 ? 1 : max_m;
+    int ld = maxm | 1;
+    size_t per_warp = ((size_t)maxm * ld + maxm + (maxm + 1) / 2 + 1) * sizeof(double);
+    int warps = (int)((96 * 1024) / per_warp);
+    if (warps > 8) warps = 8;
+    if (warps < 1) {
+        if (per_warp > 200 * 1024) return AIR_ERR_UNSUPPORTED;
+        warps = 1;
+    }
+    size_t smem = per_warp * warps;
+    AIR_CUDA(cudaFuncSetAttribute(lair_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int64_t blocks = (L.nc + warps - 1) / warps;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) blocks = 1;
+    lair_solve_kernel<<<air_counted((unsigned)blocks), warps * 32, smem, s>>>(L.nc, L.crows, L.rp, L.ci, L.v, L.srp, L.sci, L.cf,
+                                                                L.rrp, L.rci, L.rv, maxm, ld,
+                                                                (unsigned long long *)d_nsing);
+    AIR_LAUNCH();
+    return AIR_OK;
+}
+
+int air_onepoint_P(const AirLevel &L, double theta, cudaStream_t s) {
+    onepoint_kernel<<<air_counted(grid_for(L.n * 32, 256)), 256, 0, s>>>(L.n, L.rp, L.ci, L.v, theta, L.cf, L.cid, L.pcol);
+    AIR_LAUNCH();
+    return AIR_OK;
+}
+
+int air_rap_terms(const AirLevel &L, int32_t *terms, cudaStream_t s) {
+    rap_terms_kernel<<<air_counted(grid_for(L.nc, 256)), 256, 0, s>>>(L.nc, L.rrp, L.rci, L.rp, terms);
+    AIR_LAUNCH();
+    return AIR_OK;
+}
+
+int air_rap(const AirLevel &L, int64_t *acrp, int32_t *acci, double *acv, int32_t *cnt, int fill,
+            int32_t max_terms, cudaStream_t s) {
+    int bits = 5;
+    while ((1 << bits) < 2 * (max_terms > 1 ? max_terms : 1)) ++bits;
+    size_t per_warp = (size_t)(1 << bits) * 20;
+    if (per_warp > 200 * 1024) return AIR_ERR_UNSUPPORTED;
+    int warps = (int)((160 * 1024) / per_warp);
+    if (warps > 8) warps = 8;
+    if (warps < 1) warps = 1;
+    size_t smem = per_warp * warps;
+    int64_t blocks = (L.nc + warps - 1) / warps;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) blocks = 1;
+    if (fill) {
+        AIR_CUDA(cudaFuncSetAttribute(rap_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        rap_kernel<true><<<air_counted((unsigned)blocks), warps * 32, smem, s>>>(L.nc, L.rrp, L.rci, L.rv, L.rp, L.ci, L.v, L.pcol,
+                                                                   bits, nullptr, acrp, acci, acv);
+    } else {
+        AIR_CUDA(cudaFuncSetAttribute(rap_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        rap_kernel<false><<<air_counted((unsigned)blocks), warps * 32, smem, s>>>(L.nc, L.rrp, L.rci, L.rv, L.rp, L.ci, L.v, L.pcol,
+                                                                    bits, cnt, nullptr, nullptr, nullptr);
+    }
+    AIR_LAUNCH();
+    return AIR_OK;
+}
+
+// inv: n*n row major.  work: 2*n*n + n + 1 doubles.
+int air_coarse_inverse(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, double *inv, double *work,
+                       int *d_err, cudaStream_t s) {
+    double *M = work, *fcol = work + 2 * n * n, *amax = fcol + n;
+    AIR_CUDA(cudaMemsetAsync(M, 0, (size_t)(2 * n * n) * sizeof(double), s));
+    dense_scatter_kernel<<<air_counted(grid_for(n, 256)), 256, 0, s>>>(n, rp, ci, v, M);
+    dense_absmax_kernel<<<air_counted(1), 1024, 0, s>>>(n, M, amax);
+    AIR_LAUNCH();
+    unsigned eg = grid_for(n * 2 * n, 256, 152 * 8);
+    for (int64_t k = 0; k < n; ++k) {
+        gj_pivot_kernel<<<air_counted(1), 1024, 0, s>>>(n, k, M, fcol, amax, d_err);
+        gj_eliminate_kernel<<<air_counted(eg), 256, 0, s>>>(n, k, M, fcol, d_err);
+    }
+    AIR_LAUNCH();
+    dense_extract_kernel<<<air_counted(grid_for(n * n, 256)), 256, 0, s>>>(n, M, inv);
+    AIR_LAUNCH();
+    return AIR_OK;
+}

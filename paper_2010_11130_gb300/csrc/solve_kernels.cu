@@ -1,0 +1,507 @@
+// Solve-phase kernels: CSR SpMV, the V-cycle (restriction, coarsest dense
+// solve, one-point interpolation fused into the first relaxation sweep,
+// masked Jacobi sweeps) and the GMRES building blocks (block-partial multi-dot
+// products fused with the Gram-Schmidt updates, device-side Givens rotations).
+//
+// The V-cycle is x = 0 on every level, b_{l+1} = R_l b_l, x_L = A_L^{-1} b_L,
+// x_l = P_l x_{l+1} followed by Jacobi sweeps over the point sets of the
+// relaxation pattern (arXiv:2010.11130, Section 3; FCF-Jacobi replaces the
+// paper's forward Gauss-Seidel of Section 4).  All of it is sparse or
+// bandwidth-bound: no tensor cores.
+#include <math.h>
+#include <string.h>
+
+#include <type_traits>
+
+#include "air_internal.cuh"
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+unsigned grid_cap(int64_t items, int threads, int64_t cap = 152 * 16) {
+    int64_t b = (items + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > cap) b = cap;
+    return (unsigned)b;
+}
+
+template <typename T>
+struct Acc;
+template <>
+struct Acc<double> { using type = double; };
+template <>
+struct Acc<float> { using type = float; };
+
+template <int VL, typename A>
+__device__ __forceinline__ A seg_sum(A s) {
+#pragma unroll
+    for (int o = VL / 2; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o, VL);
+    return s;
+}
+
+// y = A x   or   y = b - A x      (VL lanes per row)
+template <int VL, typename TV, typename TX>
+__global__ void __launch_bounds__(256) spmv_kernel(int64_t n, const int64_t *__restrict__ rp,
+                                                   const int32_t *__restrict__ ci, const TV *__restrict__ v,
+                                                   const TX *__restrict__ x, TX *__restrict__ y,
+                                                   const TX *__restrict__ b) {
+    using A = typename Acc<TX>::type;
+    int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / VL;
+    int lane = threadIdx.x & (VL - 1);
+    int64_t ng = ((int64_t)gridDim.x * blockDim.x) / VL;
+    for (int64_t row = g; row < n; row += ng) {
+        A s = 0;
+        for (int64_t e = rp[row] + lane; e < rp[row + 1]; e += VL) s += (A)v[e] * (A)x[ci[e]];
+        s = seg_sum<VL, A>(s);
+        if (lane == 0) y[row] = b ? (TX)((A)b[row] - s) : (TX)s;
+    }
+}
+
+// One masked Jacobi sweep: rows with cf == which get
+//     x_new_i = x_i + omega (b_i - (A x)_i) / a_ii,
+// the others x_new_i = x_i.  With INTERP the input iterate is x = P x_c,
+// evaluated on the fly from the coarse vector through pcol (one-point P).
+template <int VL, typename T, bool INTERP>
+__global__ void __launch_bounds__(256) jacobi_kernel(int64_t n, const int64_t *__restrict__ rp,
+                                                     const int32_t *__restrict__ ci, const T *__restrict__ v,
+                                                     const T *__restrict__ dinv, const int8_t *__restrict__ cf,
+                                                     int which, T omega, const T *__restrict__ b,
+                                                     const T *__restrict__ xin, const int32_t *__restrict__ pcol,
+                                                     T *__restrict__ xout) {
+    int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / VL;
+    int lane = threadIdx.x & (VL - 1);
+    int64_t ng = ((int64_t)gridDim.x * blockDim.x) / VL;
+    for (int64_t row = g; row < n; row += ng) {
+        T xi;
+        if (INTERP) {
+            int32_t pc = pcol[row];
+            xi = pc >= 0 ? xin[pc] : (T)0;
+        } else {
+            xi = xin[row];
+        }
+        if (cf[row] != which) {
+            if (lane == 0) xout[row] = xi;
+            continue;
+        }
+        T s = 0;
+        for (int64_t e = rp[row] + lane; e < rp[row + 1]; e += VL) {
+            int32_t j = ci[e];
+            T xj;
+            if (INTERP) {
+                int32_t pc = pcol[j];
+                xj = pc >= 0 ? xin[pc] : (T)0;
+            } else {
+                xj = xin[j];
+            }
+            s += v[e] * xj;
+        }
+        s = seg_sum<VL, T>(s);
+        if (lane == 0) xout[row] = xi + omega * (b[row] - s) * dinv[row];
+    }
+}
+
+template <typename T>
+__global__ void interp_kernel(int64_t n, const int32_t *pcol, const T *xc, T *x) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t pc = pcol[i];
+        x[i] = pc >= 0 ? xc[pc] : (T)0;
+    }
+}
+
+// x = Cinv b, dense row-major, one warp per row
+template <typename T>
+__global__ void dense_gemv_kernel(int64_t n, const T *__restrict__ Ci, const T *__restrict__ b, T *__restrict__ x) {
+    int lane = threadIdx.x & 31;
+    int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = w; r < n; r += nw) {
+        T s = 0;
+        for (int64_t c = lane; c < n; c += 32) s += Ci[r * n + c] * b[c];
+        s = seg_sum<32, T>(s);
+        if (lane == 0) x[r] = s;
+    }
+}
+
+__global__ void d2f_kernel(const double *in, float *out, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (float)in[i];
+}
+
+__global__ void f2d_kernel(const float *in, double *out, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (double)in[i];
+}
+
+__global__ void diag_inverse_kernel(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, double *dinv,
+                                    float *dinv32) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double d = 0.0;
+        for (int64_t k = rp[i]; k < rp[i + 1]; ++k)
+            if (ci[k] == i) { d = v[k]; break; }
+        double r = 1.0 / d;
+        dinv[i] = r;
+        if (dinv32) dinv32[i] = (float)r;
+    }
+}
+
+// ------------------------------------------------------------------ GMRES
+constexpr int RT = 256;          // threads of the reduction kernels
+constexpr int MAXK = AIR_MAX_RESTART + 1;
+
+// partials[i * nblk + blk] = sum over this block's slice of V_i . w   (i < k)
+template <int KB>
+__global__ void __launch_bounds__(RT) dot_partials_kernel(int64_t n, const double *__restrict__ V, int64_t ldv,
+                                                          int k0, int k, const double *__restrict__ w,
+                                                          double *__restrict__ partials, int nblk) {
+    __shared__ double red[RT / 32][KB];
+    double acc[KB];
+#pragma unroll
+    for (int i = 0; i < KB; ++i) acc[i] = 0.0;
+    for (int64_t t = (int64_t)blockIdx.x * RT + threadIdx.x; t < n; t += (int64_t)gridDim.x * RT) {
+        double wt = w[t];
+#pragma unroll
+        for (int i = 0; i < KB; ++i)
+            if (k0 + i < k) acc[i] += V[(int64_t)(k0 + i) * ldv + t] * wt;
+    }
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < KB; ++i) {
+        double s = acc[i];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+        if (lane == 0) red[wid][i] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < KB && k0 + (int)threadIdx.x < k) {
+        double s = 0.0;
+        for (int q = 0; q < RT / 32; ++q) s += red[q][threadIdx.x];
+        partials[(int64_t)(k0 + threadIdx.x) * nblk + blockIdx.x] = s;
+    }
+}
+
+// w -= sum_i h_i V_i (i < k); then partial dots of the updated w with V_i
+// (i < dots) or, if dots == -1, the partial squared norm of w into row 0.
+template <int KB>
+__global__ void __launch_bounds__(RT) update_dot_kernel(int64_t n, const double *__restrict__ V, int64_t ldv, int k,
+                                                        const double *__restrict__ h, double *__restrict__ w,
+                                                        double *__restrict__ partials, int nblk, int dots) {
+    __shared__ double red[RT / 32][KB];
+    __shared__ double hs[KB];
+    if (threadIdx.x < KB) hs[threadIdx.x] = (int)threadIdx.x < k ? h[threadIdx.x] : 0.0;
+    __syncthreads();
+    double acc[KB];
+#pragma unroll
+    for (int i = 0; i < KB; ++i) acc[i] = 0.0;
+    for (int64_t t = (int64_t)blockIdx.x * RT + threadIdx.x; t < n; t += (int64_t)gridDim.x * RT) {
+        double vt[KB];
+        double wt = w[t];
+#pragma unroll
+        for (int i = 0; i < KB; ++i) {
+            vt[i] = i < k ? V[(int64_t)i * ldv + t] : 0.0;
+            wt -= hs[i] * vt[i];
+        }
+        w[t] = wt;
+        if (dots < 0) {
+            acc[0] += wt * wt;
+        } else {
+#pragma unroll
+            for (int i = 0; i < KB; ++i) acc[i] += vt[i] * wt;
+        }
+    }
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int nd = dots < 0 ? 1 : dots;
+#pragma unroll
+    for (int i = 0; i < KB; ++i) {
+        double s = acc[i];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+        if (lane == 0) red[wid][i] = s;
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < nd && (int)threadIdx.x < KB) {
+        double s = 0.0;
+        for (int q = 0; q < RT / 32; ++q) s += red[q][threadIdx.x];
+        partials[(int64_t)threadIdx.x * nblk + blockIdx.x] = s;
+    }
+}
+
+__global__ void reduce_partials_kernel(const double *partials, int nblk, double *out) {
+    __shared__ double red[32];
+    const double *p = partials + (int64_t)blockIdx.x * nblk;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nblk; i += blockDim.x) s += p[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(FULL, t, o);
+        if (threadIdx.x == 0) out[blockIdx.x] = t;
+    }
+}
+
+// out = in / d, with d = *dn (or sqrt(*dn) if sqrt_of)
+__global__ void scale_kernel(int64_t n, const double *in, double *out, const double *dn, int sqrt_of) {
+    double d = sqrt_of ? sqrt(*dn) : *dn;
+    double r = d != 0.0 ? 1.0 / d : 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = in[i] * r;
+}
+
+// Column j of the Hessenberg matrix from the two Gram-Schmidt passes, the
+// rotations, and the residual estimate |g_{j+1}| / ||b||.
+__global__ void givens_kernel(int j, int m, const double *h1, const double *h2, const double *nrm2, double *Hm,
+                              double *cs, double *sn, double *g, double *scal, double bnorm) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double *col = Hm + (int64_t)j * (m + 1);
+    for (int i = 0; i <= j; ++i) col[i] = h1[i] + h2[i];
+    double hn = sqrt(*nrm2);
+    col[j + 1] = hn;
+    for (int i = 0; i < j; ++i) {
+        double a = col[i], c = col[i + 1];
+        col[i] = cs[i] * a + sn[i] * c;
+        col[i + 1] = -sn[i] * a + cs[i] * c;
+    }
+    double a = col[j], c = col[j + 1];
+    double r = hypot(a, c);
+    cs[j] = r > 0.0 ? a / r : 1.0;
+    sn[j] = r > 0.0 ? c / r : 0.0;
+    col[j] = r;
+    col[j + 1] = 0.0;
+    g[j + 1] = -sn[j] * g[j];
+    g[j] = cs[j] * g[j];
+    scal[1] = fabs(g[j + 1]) / bnorm;
+    scal[2] = hn;
+}
+
+__global__ void hessenberg_solve_kernel(int k, int m, const double *Hm, const double *g, double *y) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (int i = k - 1; i >= 0; --i) {
+        double s = g[i];
+        for (int c = i + 1; c < k; ++c) s -= Hm[(int64_t)c * (m + 1) + i] * y[c];
+        y[i] = s / Hm[(int64_t)i * (m + 1) + i];
+    }
+}
+
+__global__ void axpy_multi_kernel(int64_t n, const double *__restrict__ Z, int64_t ldz, int k,
+                                  const double *__restrict__ y, double *__restrict__ x) {
+    __shared__ double ys[MAXK];
+    for (int i = threadIdx.x; i < k; i += blockDim.x) ys[i] = y[i];
+    __syncthreads();
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        double s = x[t];
+        for (int i = 0; i < k; ++i) s += ys[i] * Z[(int64_t)i * ldz + t];
+        x[t] = s;
+    }
+}
+
+__global__ void set_scalar_kernel(double *p, double v) { *p = v; }
+
+template <int VL, typename TV, typename TX>
+void launch_spmv(int64_t n, const int64_t *rp, const int32_t *ci, const TV *v, const TX *x, TX *y, const TX *b,
+                 cudaStream_t s) {
+    unsigned g = grid_cap(n * VL, 256, 152 * 64);
+    spmv_kernel<VL, TV, TX><<<air_counted(g), 256, 0, s>>>(n, rp, ci, v, x, y, b);
+}
+
+template <typename TV, typename TX>
+void spmv_dispatch(int64_t n, int64_t nnz, const int64_t *rp, const int32_t *ci, const TV *v, const TX *x, TX *y,
+                   const TX *b, cudaStream_t s) {
+    double avg = n > 0 ? (double)nnz / (double)n : 0.0;
+    if (avg <= 4) launch_spmv<2>(n, rp, ci, v, x, y, b, s);
+    else if (avg <= 10) launch_spmv<4>(n, rp, ci, v, x, y, b, s);
+    else if (avg <= 40) launch_spmv<8>(n, rp, ci, v, x, y, b, s);
+    else launch_spmv<16>(n, rp, ci, v, x, y, b, s);
+}
+
+template <int VL, typename T, bool INTERP>
+void launch_jacobi(const AirLevel &L, const T *v, const T *dinv, int which, T omega, const T *b, const T *xin,
+                   T *xout, cudaStream_t s) {
+    unsigned g = grid_cap(L.n * VL, 256, 152 * 64);
+    jacobi_kernel<VL, T, INTERP><<<air_counted(g), 256, 0, s>>>(L.n, L.rp, L.ci, v, dinv, L.cf, which, omega, b, xin, L.pcol,
+                                                   xout);
+}
+
+template <typename T, bool INTERP>
+void jacobi_dispatch(const AirLevel &L, const T *v, const T *dinv, int which, T omega, const T *b, const T *xin,
+                     T *xout, cudaStream_t s) {
+    double avg = L.n > 0 ? (double)L.nnz / (double)L.n : 0.0;
+    if (avg <= 4) launch_jacobi<2, T, INTERP>(L, v, dinv, which, omega, b, xin, xout, s);
+    else if (avg <= 10) launch_jacobi<4, T, INTERP>(L, v, dinv, which, omega, b, xin, xout, s);
+    else if (avg <= 40) launch_jacobi<8, T, INTERP>(L, v, dinv, which, omega, b, xin, xout, s);
+    else launch_jacobi<16, T, INTERP>(L, v, dinv, which, omega, b, xin, xout, s);
+}
+
+template <typename T>
+const T *lvl_vals(const AirLevel &L);
+template <>
+const double *lvl_vals<double>(const AirLevel &L) { return L.v; }
+template <>
+const float *lvl_vals<float>(const AirLevel &L) { return L.v32; }
+template <typename T>
+const T *lvl_dinv(const AirLevel &L);
+template <>
+const double *lvl_dinv<double>(const AirLevel &L) { return L.dinv; }
+template <>
+const float *lvl_dinv<float>(const AirLevel &L) { return L.dinv32; }
+template <typename T>
+const T *lvl_rvals(const AirLevel &L);
+template <>
+const double *lvl_rvals<double>(const AirLevel &L) { return L.rv; }
+template <>
+const float *lvl_rvals<float>(const AirLevel &L) { return L.rv32; }
+
+// V-cycle in precision T.  b0: finest right-hand side, x0: finest output.
+template <typename T>
+int vcycle_t(const air_hierarchy *H, const T *b0, T *x0, cudaStream_t s) {
+    int L = H->nlev;
+    const char *relax = H->opt.relax;
+    int ns = (int)strnlen(relax, sizeof(H->opt.relax));
+    T omega = (T)H->opt.omega;
+    // restriction down to the coarsest level
+    for (int l = 0; l + 1 < L; ++l) {
+        const AirLevel &A = H->lev[l];
+        const T *bl = l == 0 ? b0 : (const T *)A.b;
+        spmv_dispatch<T, T>(A.nc, A.nnz_r, A.rrp, A.rci, lvl_rvals<T>(A), bl, (T *)H->lev[l + 1].b, nullptr, s);
+    }
+    // coarsest: x = A_L^{-1} b
+    {
+        const AirLevel &C = H->lev[L - 1];
+        const T *bl = L == 1 ? b0 : (const T *)C.b;
+        T *xl = L == 1 ? x0 : (T *)C.x;
+        const T *Ci = std::is_same<T, double>::value ? (const T *)H->cinv : (const T *)H->cinv32;
+        unsigned g = grid_cap(C.n * 32, 256, 152 * 8);
+        dense_gemv_kernel<T><<<air_counted(g), 256, 0, s>>>(C.n, Ci, bl, xl);
+    }
+    // interpolation and relaxation back up
+    for (int l = L - 2; l >= 0; --l) {
+        const AirLevel &A = H->lev[l];
+        const T *bl = l == 0 ? b0 : (const T *)A.b;
+        T *out = l == 0 ? x0 : (T *)A.x;
+        T *alt = (T *)A.x2;
+        const T *xc = (const T *)H->lev[l + 1].x;
+        if (ns == 0) {
+            interp_kernel<T><<<air_counted(grid_cap(A.n, 256)), 256, 0, s>>>(A.n, A.pcol, xc, out);
+            continue;
+        }
+        const T *v = lvl_vals<T>(A);
+        const T *dinv = lvl_dinv<T>(A);
+        const T *cur = xc;
+        for (int q = 0; q < ns; ++q) {
+            T *dst = ((ns - 1 - q) % 2 == 0) ? out : alt;
+            int which = relax[q] == 'C' ? 1 : 0;
+            if (q == 0)
+                jacobi_dispatch<T, true>(A, v, dinv, which, omega, bl, cur, dst, s);
+            else
+                jacobi_dispatch<T, false>(A, v, dinv, which, omega, bl, cur, dst, s);
+            cur = dst;
+        }
+    }
+    AIR_LAUNCH();
+    return AIR_OK;
+}
+
+}  // namespace
+
+int air_spmv_f64(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, const double *x, double *y,
+                 const double *b, cudaStream_t s) {
+    // 8 lanes per row: the trace systems hold 9 to 61 entries per row.
+    launch_spmv<8, double, double>(n, rp, ci, v, x, y, b, s);
+    AIR_LAUNCH();
+    return AIR_OK;
+}
+
+int air_vcycle_run(const air_hierarchy *H, const double *b, double *x, cudaStream_t s) {
+    if (H->opt.precision == AIR_PREC_F64) return vcycle_t<double>(H, b, x, s);
+    const AirLevel &L0 = H->lev[0];
+    float *b32 = (float *)L0.b, *x32 = (float *)L0.x;
+    d2f_kernel<<<air_counted(grid_cap(L0.n, 256)), 256, 0, s>>>(b, b32, L0.n);
+    AIR_TRY(vcycle_t<float>(H, b32, x32, s));
+    f2d_kernel<<<air_counted(grid_cap(L0.n, 256)), 256, 0, s>>>(x32, x, L0.n);
+    AIR_LAUNCH();
+    return AIR_OK;
+}
+
+int air_cast_d2f(const double *in, float *out, int64_t n, cudaStream_t s) {
+    d2f_kernel<<<air_counted(grid_cap(n, 256)), 256, 0, s>>>(in, out, n);
+    AIR_LAUNCH();
+    return AIR_OK;
+}
+
+int air_diag_inverse(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, double *dinv, float *dinv32,
+                     cudaStream_t s) {
+    diag_inverse_kernel<<<air_counted(grid_cap(n, 256)), 256, 0, s>>>(n, rp, ci, v, dinv, dinv32);
+    AIR_LAUNCH();
+    return AIR_OK;
+}
+
+int air_reduce_nblk(int64_t n) {
+    int64_t b = (n + RT * 8 - 1) / (RT * 8);
+    if (b > 152 * 4) b = 152 * 4;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+int air_dot_partials(int64_t n, const double *V, int64_t ldv, int k, const double *w, double *partials, int nblk,
+                     cudaStream_t s) {
+    for (int k0 = 0; k0 < k; k0 += 16) {
+        if (k - k0 <= 4) dot_partials_kernel<4><<<air_counted(nblk), RT, 0, s>>>(n, V, ldv, k0, k, w, partials, nblk);
+        else if (k - k0 <= 8) dot_partials_kernel<8><<<air_counted(nblk), RT, 0, s>>>(n, V, ldv, k0, k, w, partials, nblk);
+        else dot_partials_kernel<16><<<air_counted(nblk), RT, 0, s>>>(n, V, ldv, k0, k, w, partials, nblk);
+    }
+    AIR_LAUNCH();
+    return AIR_OK;
+}
+
+int air_update_dot_partials(int64_t n, const double *V, int64_t ldv, int k, const double *h, double *w,
+                            double *partials, int nblk, int dots, cudaStream_t s) {
+    if (k <= 4) update_dot_kernel<4><<<air_counted(nblk), RT, 0, s>>>(n, V, ldv, k, h, w, partials, nblk, dots);
+    else if (k <= 8) update_dot_kernel<8><<<air_counted(nblk), RT, 0, s>>>(n, V, ldv, k, h, w, partials, nblk, dots);
+    else if (k <= 16) update_dot_kernel<16><<<air_counted(nblk), RT, 0, s>>>(n, V, ldv, k, h, w, partials, nblk, dots);
+    else if (k <= 32) update_dot_kernel<32><<<air_counted(nblk), RT, 0, s>>>(n, V, ldv, k, h, w, partials, nblk, dots);
+    else return AIR_ERR_UNSUPPORTED;
+    AIR_LAUNCH();
+    return AIR_OK;
+}
+
+int air_reduce_partials(int k, const double *partials, int nblk, double *out, cudaStream_t s) {
+    if (k <= 0) return AIR_OK;
+    reduce_partials_kernel<<<air_counted(k), 256, 0, s>>>(partials, nblk, out);
+    AIR_LAUNCH();
+    return AIR_OK;
+}
+
+int air_scale_vec(int64_t n, const double *in, double *out, const double *d_norm, int sqrt_of, cudaStream_t s) {
+    scale_kernel<<<air_counted(grid_cap(n, 256)), 256, 0, s>>>(n, in, out, d_norm, sqrt_of);
+    AIR_LAUNCH();
+    return AIR_OK;
+}
+
+int air_arnoldi_givens(int j, int m, const double *h1, const double *h2, const double *nrm2, double *Hm, double *cs,
+                       double *sn, double *g, double *scal, double bnorm, cudaStream_t s) {
+    givens_kernel<<<air_counted(1), 32, 0, s>>>(j, m, h1, h2, nrm2, Hm, cs, sn, g, scal, bnorm);
+    AIR_LAUNCH();
+    return AIR_OK;
+}
+
+int air_hessenberg_solve(int k, int m, const double *Hm, const double *g, double *y, cudaStream_t s) {
+    hessenberg_solve_kernel<<<air_counted(1), 32, 0, s>>>(k, m, Hm, g, y);
+    AIR_LAUNCH();
+    return AIR_OK;
+}
+
+int air_axpy_multi(int64_t n, const double *Z, int64_t ldz, int k, const double *y, double *x, cudaStream_t s) {
+    axpy_multi_kernel<<<air_counted(grid_cap(n, 256)), 256, 0, s>>>(n, Z, ldz, k, y, x);
+    AIR_LAUNCH();
+    return AIR_OK;
+}
+
+int air_fill_zero(double *x, int64_t n, cudaStream_t s) {
+    AIR_CUDA(cudaMemsetAsync(x, 0, (size_t)n * sizeof(double), s));
+    return AIR_OK;
+}
+
+int air_set_scalar(double *p, double v, cudaStream_t s) {
+    set_scalar_kernel<<<air_counted(1), 1, 0, s>>>(p, v);
+    AIR_LAUNCH();
+    return AIR_OK;
+}

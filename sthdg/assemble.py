@@ -86,6 +86,7 @@ class Problem:
     elem_velocity: Optional[np.ndarray] = None       # (E, D-1) piecewise-constant override
     alpha: Optional[float] = None
     name: str = ""
+    spec: Optional[tuple] = None                     # (factory name, kwargs) to rebuild in a worker
 
 
 @dataclass
@@ -228,8 +229,41 @@ def dirichlet_values(mesh: Mesh, prob: Problem, ref: RefData) -> np.ndarray:
     return lam
 
 
+def _condense_chunk(mesh: Mesh, prob: Problem, ref: RefData, e: np.ndarray, keep_local: bool):
+    A, B, C, Dm, Fv, Gv = element_matrices(mesh, prob, ref, e)
+    rhs = np.concatenate([B, Fv[:, :, None]], axis=2)
+    X = np.linalg.solve(A, rhs)                      # A^{-1} [B, F]
+    S = Dm - C @ X[:, :, :-1]
+    H = Gv - np.einsum("emi,ei->em", C, X[:, :, -1])
+    nf, b = mesh.D + 1, ref.b
+    SK = S.reshape(len(e), nf, b, nf, b).transpose(0, 1, 3, 2, 4)
+    HK = H.reshape(len(e), nf, b)
+    loc = (X[:, :, :-1], X[:, :, -1]) if keep_local else None
+    return SK, HK, loc
+
+
+_WORKER_STATE = {}
+
+
+def _worker_chunk(spec, start, stop):
+    """Process-pool task: rebuild the problem and mesh from spec (cached per
+    worker), condense elements [start, stop)."""
+    from . import problems
+    from .mesh import build_mesh
+    key = repr(spec)
+    if _WORKER_STATE.get("key") != key:
+        prob = problems.make(spec)
+        mesh = build_mesh(prob.D, prob.n, reflect=prob.reflect, lower=prob.lower, upper=prob.upper,
+                          vertex_map=prob.vertex_map)
+        _WORKER_STATE.update(key=key, prob=prob, mesh=mesh, ref=RefData(prob.D, prob.p))
+    st = _WORKER_STATE
+    SK, HK, _ = _condense_chunk(st["mesh"], st["prob"], st["ref"], np.arange(start, stop), False)
+    return start, stop, SK, HK
+
+
 def assemble(prob: Problem, mesh: Optional[Mesh] = None, chunk: int = 16384,
-             keep_local: bool = False, scale: bool = True, keep_diag: bool = False) -> TraceSystem:
+             keep_local: bool = False, scale: bool = True, keep_diag: bool = False,
+             workers: int = 1) -> TraceSystem:
     """Assemble, condense and block-scale; returns the trace system in CSR.
 
     Free facets keep the global (sorted-vertex) facet order; DOF = r*b + m for
@@ -251,18 +285,25 @@ def assemble(prob: Problem, mesh: Optional[Mesh] = None, chunk: int = 16384,
     SK = np.empty((E, nf, nf, b, b))
     HK = np.empty((E, nf, b))
     local = (np.empty((E, ref.nb, nf * b)), np.empty((E, ref.nb))) if keep_local else None
-    for s in range(0, E, chunk):
-        e = np.arange(s, min(E, s + chunk))
-        A, B, C, Dm, Fv, Gv = element_matrices(mesh, prob, ref, e)
-        rhs = np.concatenate([B, Fv[:, :, None]], axis=2)
-        X = np.linalg.solve(A, rhs)                      # A^{-1} [B, F]
-        S = Dm - C @ X[:, :, :-1]
-        H = Gv - np.einsum("emi,ei->em", C, X[:, :, -1])
-        SK[e] = S.reshape(len(e), nf, b, nf, b).transpose(0, 1, 3, 2, 4)
-        HK[e] = H.reshape(len(e), nf, b)
-        if keep_local:
-            local[0][e] = X[:, :, :-1]
-            local[1][e] = X[:, :, -1]
+    if workers > 1 and prob.spec is not None and not keep_local and prob.elem_velocity is None:
+        import multiprocessing as mp
+        from concurrent.futures import ProcessPoolExecutor
+        bounds = [(s0, min(E, s0 + chunk)) for s0 in range(0, E, chunk)]
+        with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+            futs = [ex.submit(_worker_chunk, prob.spec, a, z) for a, z in bounds]
+            for f in futs:
+                a, z, SKc, HKc = f.result()
+                SK[a:z] = SKc
+                HK[a:z] = HKc
+    else:
+        for s0 in range(0, E, chunk):
+            e = np.arange(s0, min(E, s0 + chunk))
+            SKc, HKc, loc = _condense_chunk(mesh, prob, ref, e, keep_local)
+            SK[e] = SKc
+            HK[e] = HKc
+            if keep_local:
+                local[0][e] = loc[0]
+                local[1][e] = loc[1]
     lamD = dirichlet_values(mesh, prob, ref)
 
     kind = mesh.facet_kind

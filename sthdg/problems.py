@@ -30,7 +30,8 @@ def manufactured_1d(n: int = 32, p: int = 1, nu: float = 1e-4, a: float = 1.0) -
     return Problem(D=2, n=n, p=p, nu=nu,
                    velocity=lambda X: np.full(X.shape[:-1] + (1,), a),
                    source=f, g_dirichlet=u, u_initial=u, exact=u,
-                   reflect=choose_reflection(2, [a]), name=f"mms1d_n{n}_p{p}")
+                   reflect=choose_reflection(2, [a]), name=f"mms1d_n{n}_p{p}",
+                   spec=("manufactured_1d", dict(n=n, p=p, nu=nu, a=a)))
 
 
 def manufactured_2d(n: int = 48, p: int = 2, nu: float = 1e-6, velocity: str = "rotating",
@@ -68,7 +69,9 @@ def manufactured_2d(n: int = 48, p: int = 2, nu: float = 1e-6, velocity: str = "
 
     return Problem(D=3, n=n, p=p, nu=nu, velocity=vel, source=f, g_dirichlet=u,
                    u_initial=u, exact=u, reflect=choose_reflection(3, amean),
-                   name=f"mms2d_{velocity}_n{n}_p{p}")
+                   name=f"mms2d_{velocity}_n{n}_p{p}",
+                   spec=("manufactured_2d", dict(n=n, p=p, nu=nu, velocity=velocity,
+                                                 a_const=tuple(np.asarray(a_const, dtype=float)))))
 
 
 def pure_advection(D: int, n: int, p: int, a=None) -> Problem:
@@ -91,7 +94,8 @@ def pure_advection(D: int, n: int, p: int, a=None) -> Problem:
     return Problem(D=D, n=n, p=p, nu=0.0,
                    velocity=lambda X: np.broadcast_to(a, X.shape[:-1] + (D - 1,)).copy(),
                    source=lambda X: np.zeros(X.shape[:-1]), g_dirichlet=u, u_initial=u,
-                   exact=u, reflect=choose_reflection(D, a), name=f"adv{D}d_n{n}_p{p}")
+                   exact=u, reflect=choose_reflection(D, a), name=f"adv{D}d_n{n}_p{p}",
+                   spec=("pure_advection", dict(D=D, n=n, p=p, a=tuple(a.tolist()))))
 
 
 def rotating_pulse(n: int, p: int, nu: float, A: float = 0.1) -> Problem:
@@ -120,7 +124,15 @@ def rotating_pulse(n: int, p: int, nu: float, A: float = 0.1) -> Problem:
                    velocity=lambda X: np.stack([-4 * X[..., 2], 4 * X[..., 1]], axis=-1),
                    source=lambda X: np.zeros(X.shape[:-1]), g_dirichlet=u, u_initial=u,
                    exact=u, reflect=(0, 0, 0), lower=(0.0, -0.5, -0.5), upper=(1.0, 0.5, 0.5),
-                   vertex_map=vmap, name=f"pulse_n{n}_p{p}")
+                   vertex_map=vmap, name=f"pulse_n{n}_p{p}",
+                   spec=("rotating_pulse", dict(n=n, p=p, nu=nu, A=A)))
+
+
+def make(spec) -> Problem:
+    """Rebuild a problem from its (factory name, kwargs) spec."""
+    name, kw = spec
+    return {"manufactured_1d": manufactured_1d, "manufactured_2d": manufactured_2d,
+            "pure_advection": pure_advection, "rotating_pulse": rotating_pulse}[name](**kw)
 
 
 def workload(name: str, **kw) -> Problem:
