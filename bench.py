@@ -1,0 +1,374 @@
+#!/usr/bin/env python
+"""AIR-GMRES time-to-1e-8 (setup + solve) and V-cycle HBM bandwidth on GB300.
+
+Workload: the statically condensed, block-scaled space-time HDG trace system
+of 2D+time advection-diffusion on [0,1]^3 split into 48^3 cubes x 6
+tetrahedra, p = 2 (7,934,976 unknowns), rotating velocity
+a = (-(y-1/2), x-1/2), nu = 1e-6, manufactured u = sin(pi x) sin(pi y)
+cos(2 pi t).  Synthetic and seeded; built on the host before timing.
+
+One step = air_setup (strength, C/F splitting, l-AIR restriction, one-point
+interpolation, Galerkin products on every level, coarsest inverse) plus
+air_gmres_solve to ||b - A x|| / ||b|| <= 1e-8, with A and b resident in HBM.
+It is timed for the FP32 hierarchy inside FP64 flexible GMRES (the reported
+value) and for the plain FP64 hierarchy (reported alongside).  The V-cycle
+and the SpMV are timed separately for the roofline.
+
+--impl reference times the CPU oracle (oracle/air_oracle.c, single thread)
+on a bounded sample of the same workload family and scales it to the full
+workload by the unknown count (the method costs O(N) per iteration).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "AIR-GMRES time-to-1e-8 (setup+solve s) and V-cycle HBM GB/s, FP32-precond vs FP64"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=48)
+    ap.add_argument("--p", type=int, default=2)
+    ap.add_argument("--nu", type=float, default=1e-6)
+    ap.add_argument("--rtol", type=float, default=1e-8)
+    ap.add_argument("--workers", type=int, default=min(16, os.cpu_count() or 1))
+    ap.add_argument("--sample-n", type=int, default=20, help="oracle sample mesh size")
+    ap.add_argument("--vcycles", type=int, default=20)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def workload_config(args):
+    n, p = args.n, args.p
+    return {"workload": f"st2d_hdg_n{n}_p{p}_rotating_nu{args.nu:g}",
+            "mesh": f"{n}^3 cubes x 6 tetrahedra", "p": p, "nu": args.nu, "rtol": args.rtol,
+            "unknowns": (12 * n ** 3 - 2 * n * n) * (p + 1) * (p + 2) // 2,
+            "theta": 0.25, "distance": 1, "relax": "FCF", "restart": 30,
+            "l2_flush": "inputs larger than L2 (CSR of A is several GB)"}
+
+
+def make_system(args):
+    from sthdg import assemble
+    from sthdg.problems import manufactured_2d
+    prob = manufactured_2d(n=args.n, p=args.p, nu=args.nu)
+    return assemble(prob, workers=args.workers)
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.rows, self.proc, self.index = [], None, index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                mx.append(float(r[1]))
+                for k, nm in enumerate(names):
+                    if r[3 + k].lower() == "active":
+                        reasons.add(nm)
+            except Exception:
+                continue
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------- algorithmic bytes
+def vcycle_bytes(H, wbytes):
+    """Algorithmic DRAM bytes of one V-cycle: each array read once per use.
+
+    Per non-coarsest level (n rows, nnz z = z_F + z_C, R with nnz_R entries,
+    n_C coarse points, w = value bytes):
+      restriction   nnz_R (w+4) + 8 n_C + w n + w n_C
+      F sweep (+P)  z_F (w+4) + 8 n_F + 4 n + w n_C + 2 w n_F + n + w n
+      C sweep       z_C (w+4) + 8 n_C + w n + 2 w n_C + n + w n
+      F sweep       z_F (w+4) + 8 n_F + w n + 2 w n_F + n + w n
+    coarsest: w n_L^2 + 2 w n_L.
+    """
+    total = 0
+    L = H.levels()
+    for l in range(L):
+        inf = H.info(l)
+        n = inf.n
+        if inf.coarsest:
+            total += wbytes * n * n + 2 * wbytes * n
+            continue
+        rp = H.export(l, "A.row_ptr")
+        cf = H.export(l, "cf").astype(bool)
+        rl = np.diff(rp)
+        zc = int(rl[cf].sum())
+        zf = int(rl[~cf].sum())
+        nc = int(cf.sum())
+        nf = n - nc
+        w = wbytes
+        total += inf.nnz_r * (w + 4) + 8 * nc + w * n + w * nc
+        total += zf * (w + 4) + 8 * nf + 4 * n + w * nc + 2 * w * nf + n + w * n
+        total += zc * (w + 4) + 8 * nc + w * n + 2 * w * nc + n + w * n
+        total += zf * (w + 4) + 8 * nf + w * n + 2 * w * nf + n + w * n
+    return total
+
+
+def spmv_bytes(n, nnz):
+    return nnz * 12 + (n + 1) * 8 + n * 8 + n * 8
+
+
+# ------------------------------------------------------------------ oracle
+_SAMPLE = {}
+
+
+def oracle_sample(args, steps=1):
+    """CPU oracle (single thread) on a bounded sample of the workload family:
+    same p, nu, velocity and source on an n_s^3 mesh; setup + GMRES to rtol.
+    Returns seconds per full solve scaled to the full workload by unknowns."""
+    import oracle
+    from sthdg import assemble
+    from sthdg.problems import manufactured_2d
+    oracle.build()
+    key = (args.sample_n, args.p, args.nu)
+    if key not in _SAMPLE:
+        _SAMPLE[key] = assemble(manufactured_2d(n=args.sample_n, p=args.p, nu=args.nu), workers=1)
+    s = _SAMPLE[key]
+    full_n = workload_config(args)["unknowns"]
+    times = []
+    its = None
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        H = oracle.setup(s.row_ptr, s.col, s.val, theta=0.25, distance=1, max_coarse=1000)
+        x, its, rr, ok, _ = oracle.gmres(s.row_ptr, s.col, s.val, H, s.rhs, rtol=args.rtol)
+        times.append(time.perf_counter() - t0)
+        del H
+    scale = full_n / s.n
+    return {"value": float(np.mean(times)) * scale, "unit": "s", "cores": 1, "kind": "oracle",
+            "sample": (f"st2d n={args.sample_n} p={args.p} nu={args.nu:g} ({s.n} unknowns, oracle "
+                       f"setup+GMRES {np.mean(times):.2f} s, {its} iterations), scaled x{scale:.2f} "
+                       f"by unknowns to {full_n}"),
+            "sample_seconds": float(np.mean(times))}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_sample(args, 1)
+    t0 = time.perf_counter()
+    vals = [oracle_sample(args, 1) for _ in range(args.steps)]
+    wall = time.perf_counter() - t0
+    v = float(np.mean([r["value"] for r in vals]))
+    cpu = dict(vals[0])
+    cpu["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * wall / max(1, args.steps),
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(args), "cpu_baseline": cpu,
+            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# -------------------------------------------------------------------- ours
+def run_ours(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    # the host-side input build (and its process pool) comes before any CUDA call
+    t0 = time.perf_counter()
+    s = make_system(args)
+    gen_s = time.perf_counter() - t0
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = oracle_sample(args, 1)
+
+    import torch
+    import paper_2010_11130_gb300 as air
+    air.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    A = air.CSR.from_host(s.row_ptr, s.col, s.val, device=f"cuda:{local}")
+    b = torch.from_numpy(np.ascontiguousarray(s.rhs)).cuda()
+    stream = torch.cuda.current_stream()
+
+    def step(prec):
+        H = air.setup(A, theta=0.25, distance=1, precision=prec)
+        x, info = air.gmres_solve(A, H, b, rtol=args.rtol)
+        H.free()
+        return info
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(prec):
+        for _ in range(args.warmup):
+            step(prec)
+        barrier()
+        k0 = air.kernel_launches()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        infos = [step(prec) for _ in range(args.steps)]
+        e1.record(stream)
+        barrier()
+        ms = e0.elapsed_time(e1)
+        if dist is not None:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms / args.steps, infos, air.kernel_launches() - k0
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms32, inf32, launches32 = timed(1)
+    ms64, inf64, launches64 = timed(0)
+    clk = clocks.stop()
+
+    # V-cycle and SpMV roofline (FP32 hierarchy is the reported form)
+    gbs_peak, peak_kind = peaks()
+    rl = {}
+    for prec, key in ((1, "f32"), (0, "f64")):
+        H = air.setup(A, theta=0.25, distance=1, precision=prec)
+        vb = vcycle_bytes(H, 4 if prec == 1 else 8)
+        xv = torch.empty_like(b)
+        for _ in range(3):
+            H.vcycle(b, xv)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.vcycles):
+            H.vcycle(b, xv)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / args.vcycles / 1e3
+        rl[key] = {"bytes": vb, "s": t, "gbs": vb / t / 1e9, "levels": H.levels()}
+        H.free()
+    y = torch.empty_like(b)
+    for _ in range(3):
+        air.spmv(A, b, y)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.vcycles):
+        air.spmv(A, b, y)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_spmv = e0.elapsed_time(e1) / args.vcycles / 1e3
+    sb = spmv_bytes(s.n, s.nnz)
+
+    # end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        rp_h = torch.from_numpy(s.row_ptr).pin_memory().numpy()
+        ci_h = torch.from_numpy(s.col).pin_memory().numpy()
+        v_h = torch.from_numpy(s.val).pin_memory().numpy()
+        b_h = torch.from_numpy(np.ascontiguousarray(s.rhs)).pin_memory().numpy()
+        x_h = torch.empty(s.n, dtype=torch.float64).pin_memory().numpy()
+        Ah = air.CSR(rp_h, ci_h, v_h, s.n)
+        torch.cuda.synchronize()
+        tt = []
+        for _ in range(max(1, args.steps)):
+            t0 = time.perf_counter()
+            Hh = air.setup(Ah, theta=0.25, distance=1, precision=1)
+            _, ih = air.gmres_solve(Ah, Hh, b_h, x_h, rtol=args.rtol)
+            Hh.free()
+            tt.append(time.perf_counter() - t0)
+        h2d = s.row_ptr.nbytes + s.col.nbytes + s.val.nbytes + b_h.nbytes
+        e2e = {"value": float(np.mean(tt)), "unit": "s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(x_h.nbytes), "iters": ih.iters, "relres": ih.relres}
+
+    if rank != 0:
+        return
+    v32 = rl["f32"]
+    line = {
+        "metric": METRIC, "value": ms32 / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms32, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 hierarchy / f64 Krylov", "data": "synthetic",
+        "config": workload_config(args),
+        "variants": {
+            "f32_precond_fgmres": {"s": ms32 / 1e3, "iters": inf32[-1].iters, "relres": inf32[-1].relres,
+                                   "vcycle_gbs": v32["gbs"]},
+            "f64": {"s": ms64 / 1e3, "iters": inf64[-1].iters, "relres": inf64[-1].relres,
+                    "vcycle_gbs": rl["f64"]["gbs"]}},
+        "roofline": {"bound": "hbm", "kernel": "V-cycle (FP32 hierarchy, all levels)",
+                     "achieved": v32["gbs"], "peak": gbs_peak, "unit": "GB/s",
+                     "frac": v32["gbs"] / gbs_peak, "traffic": None,
+                     "algorithmic_bytes": v32["bytes"], "launch_s": v32["s"], "peak_kind": peak_kind},
+        "roofline_spmv": {"bound": "hbm", "kernel": "spmv_kernel<8,double,double>",
+                          "achieved": sb / t_spmv / 1e9, "peak": gbs_peak, "unit": "GB/s",
+                          "frac": sb / t_spmv / 1e9 / gbs_peak, "algorithmic_bytes": sb, "launch_s": t_spmv},
+        "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+        "gpu_launches": int(launches32),
+        "generate_s": gen_s,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()
