@@ -248,3 +248,4 @@ def gmres_solve(A: CSR, H: Hierarchy, b, x=None, rtol: float = 1e-8, stream=None
                                C.c_void_p(sp), C.byref(inf))
     _check(st, "air_gmres_solve")
     return x, inf
+
