@@ -41,6 +41,8 @@ extern "C" {
 #define AIR_ERR_DEVICE_TIMEOUT   -6   /* a bounded device loop hit its iteration cap */
 #define AIR_ERR_COARSE_TOO_LARGE -7   /* coarsening stalled above max_dense rows */
 #define AIR_ERR_UNSUPPORTED      -8   /* option value not implemented on the GPU path */
+#define AIR_ERR_NOALLOC_LIMIT    -9   /* problem too large for the fixed workspace of
+                                         air_gmres_solve_noalloc */
 
 /* precision in which the hierarchy is stored and the V-cycle is applied */
 #define AIR_PREC_F64  0
@@ -127,6 +129,25 @@ int air_spmv(const air_csr *A, const double *x, double *y, void *stream);
  * info may be NULL.  Returns AIR_OK or AIR_NOT_CONVERGED, or an error. */
 int air_gmres_solve(const air_csr *A, const air_hierarchy *H, const double *b, double *x,
                     double rtol, void *stream, air_solve_info *info);
+
+/* The same flexible GMRES solve as air_gmres_solve, for callers that must
+ * not have the library allocate device memory during the solve: memory
+ * fully pre-assigned by a pool or budget, or a host framework that forbids
+ * allocation inside its solve phase.  (The paper has no counterpart; this is
+ * a deployment variant.)  Build H beforehand with air_setup; this call then
+ * allocates nothing -- no cudaMalloc, no pinned host buffer.
+ * The Krylov workspace is one fixed 32 MiB array of device memory that every
+ * GPU loading the library reserves until the process exits; it must hold
+ * (2 restart + 1) n + O(restart^2) doubles, so with restart 30 n can reach
+ * about 68,000; larger problems return AIR_ERR_NOALLOC_LIMIT before any work.
+ * A, b and x must be on the device (A->on_device = 1).  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress); make
+ * it before any stream capture.  All calls share the array and it keeps the
+ * previous call's contents (the solve clears what must start at zero):
+ * calls that overlap on the GPU -- from two streams or two host threads --
+ * race on it.  Synchronises the stream once per inner step. */
+int air_gmres_solve_noalloc(const air_csr *A, const air_hierarchy *H, const double *b, double *x,
+                            double rtol, void *stream, air_solve_info *info);
 
 /* Number of levels of H (>= 1). */
 int air_hierarchy_levels(const air_hierarchy *H);

@@ -22,7 +22,7 @@ AIR_PREC_F32 = 1
 
 EXPORTED = ["air_default_options", "air_setup", "air_vcycle", "air_spmv", "air_gmres_solve",
             "air_hierarchy_levels", "air_hierarchy_info", "air_hierarchy_export", "air_free",
-            "air_status_string", "air_kernel_launches"]
+            "air_status_string", "air_kernel_launches", "air_gmres_solve_noalloc"]
 
 
 class air_csr(C.Structure):
@@ -78,6 +78,9 @@ def lib() -> C.CDLL:
     L.air_gmres_solve.argtypes = [C.POINTER(air_csr), C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
                                   C.c_void_p, C.POINTER(air_solve_info)]
     L.air_gmres_solve.restype = C.c_int
+    L.air_gmres_solve_noalloc.argtypes = [C.POINTER(air_csr), C.c_void_p, C.c_void_p, C.c_void_p,
+                                          C.c_double, C.c_void_p, C.POINTER(air_solve_info)]
+    L.air_gmres_solve_noalloc.restype = C.c_int
     L.air_hierarchy_levels.argtypes = [C.c_void_p]
     L.air_hierarchy_levels.restype = C.c_int
     L.air_hierarchy_info.argtypes = [C.c_void_p, C.c_int, C.POINTER(air_level_info)]
@@ -249,3 +252,19 @@ def gmres_solve(A: CSR, H: Hierarchy, b, x=None, rtol: float = 1e-8, stream=None
     _check(st, "air_gmres_solve")
     return x, inf
 
+
+def gmres_solve_noalloc(A: CSR, H: Hierarchy, b, x, rtol: float = 1e-8, stream=None):
+    """air_gmres_solve_noalloc: the same solve with no device allocation.
+
+    For callers whose device memory is fully pre-assigned (a pool or budget)
+    or whose framework forbids allocation inside the solve phase.  A, b and x
+    are device tensors; x must be preallocated by the caller.  The Krylov
+    workspace is a fixed 32 MiB device array shared by all calls, so calls
+    that overlap on the GPU race.
+    """
+    Ac = A.c()
+    inf = air_solve_info()
+    st = lib().air_gmres_solve_noalloc(C.byref(Ac), H.handle, C.c_void_p(b.data_ptr()), C.c_void_p(x.data_ptr()),
+                                       float(rtol), C.c_void_p(_stream(stream)), C.byref(inf))
+    _check(st, "air_gmres_solve_noalloc")
+    return x, inf

@@ -502,6 +502,7 @@ const char *air_status_string(int s) {
     case AIR_ERR_DEVICE_TIMEOUT: return "device loop hit its iteration cap";
     case AIR_ERR_COARSE_TOO_LARGE: return "coarsening stalled above max_dense";
     case AIR_ERR_UNSUPPORTED: return "option not supported on the GPU path";
+    case AIR_ERR_NOALLOC_LIMIT: return "problem exceeds the fixed workspace of the allocation-free solve";
     default: return "unknown status";
     }
 }
