@@ -71,6 +71,18 @@ void free_workspace(air_hierarchy *H) {
     H->ws_m = 0;
 }
 
+// First-pass kernel variant: 2 (default) exact bitmaps + two-hop lists +
+// int8 measures; 1 lazy bitmaps with L1-cached loads; 0 lazy bitmaps with
+// L2-only loads.  Set by the environment variable AIR_RS_VARIANT.
+int rs_cached() {
+    static int v = -1;
+    if (v < 0) {
+        const char *e = getenv("AIR_RS_VARIANT");
+        v = (e && (e[0] == '0' || e[0] == '1')) ? e[0] - '0' : 2;
+    }
+    return v;
+}
+
 // Build level l+1 from level l.  Returns AIR_OK with *stop = 1 when level l
 // is the coarsest.
 int coarsen(air_hierarchy *H, int l, cudaStream_t s, int *stop) {
@@ -84,17 +96,22 @@ int coarsen(air_hierarchy *H, int l, cudaStream_t s, int *stop) {
     AIR_TRY(dalloc(&L.srp, n + 1));
     AIR_TRY(air_strength(L, o.theta, nullptr, nullptr, cnt, 0, s));
     AIR_TRY(air_exclusive_scan_i32(cnt, L.srp, n, s));
+    int32_t *dmax = nullptr;
+    AIR_TRY(dalloc(&dmax, 1));
+    AIR_CUDA(cudaMemsetAsync(dmax, 0, sizeof(int32_t), s));
+    AIR_TRY(air_reduce_max_i32(cnt, n, dmax, s));
+    int32_t max_s = 0;
+    AIR_CUDA(cudaMemcpyAsync(&max_s, dmax, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     AIR_TRY(read_i64(L.srp + n, &L.nnz_s, s));
     AIR_TRY(dalloc(&L.sci, L.nnz_s));
     AIR_TRY(air_strength(L, o.theta, L.srp, L.sci, nullptr, 1, s));
     // a2 transpose
     int64_t *strp = nullptr;
-    int32_t *stci = nullptr, *dmax = nullptr;
+    int32_t *stci = nullptr;
     AIR_TRY(dalloc(&strp, n + 1));
     AIR_TRY(dalloc(&stci, L.nnz_s));
     AIR_TRY(air_transpose_pattern(n, L.nnz_s, L.srp, L.sci, strp, stci, cnt, s));
     // largest |S^T_i| (the transposed counts are still in cnt after the scatter)
-    AIR_TRY(dalloc(&dmax, 1));
     AIR_CUDA(cudaMemsetAsync(dmax, 0, sizeof(int32_t), s));
     AIR_TRY(air_reduce_max_i32(cnt, n, dmax, s));
     int32_t max_st = 0;
@@ -102,7 +119,7 @@ int coarsen(air_hierarchy *H, int l, cudaStream_t s, int *stop) {
     AIR_CUDA(cudaStreamSynchronize(s));
     // a3 C/F splitting
     AIR_TRY(dalloc(&L.cf, n));
-    AIR_TRY(air_rs_first_pass(n, L.srp, L.sci, strp, stci, max_st, L.cf, H->d_err, s));
+    AIR_TRY(air_rs_first_pass(n, L.srp, L.sci, strp, stci, max_st, max_s, L.cf, H->d_err, rs_cached(), s));
     AIR_TRY(check_err(H, s));
     dfree(strp);
     dfree(stci);

@@ -120,56 +120,103 @@ __global__ void sort_rows_kernel(int64_t n, const int64_t *rp, int32_t *ci) {
 
 // ------------------------------------------------- first-pass C/F splitting
 // Sequential Ruge-Stueben first pass (largest measure first, ties to the
-// smallest index) run by ONE thread block.  Undecided points with measure
-// lambda >= 1 live in bucket lambda of a three-level bitmap (64-bit words;
-// level 2 of every bucket is held in shared memory).  Bits are removed
-// lazily: the search validates a candidate (still undecided, measure equal
-// to the bucket) and clears stale bits it meets.  All mutable global state is
-// read with __ldcg (L2) so the single block always sees its own atomics.
-constexpr int8_t ST_F = 0, ST_C = 1, ST_U = 2;
-constexpr int RS_THREADS = 256;
+// smallest index), run exactly by ONE warp.  lam[k] holds the measure of an
+// undecided point (>= 0) or its decision (-1 = F, -2 = C), so one load
+// answers both questions.  Undecided points with measure >= 1 live in bucket
+// lambda of a three-level bitmap (64-bit words; level 2 of every bucket sits
+// in shared memory).  Bits are removed lazily: the search validates a
+// candidate (lam equal to the bucket) and clears stale bits it meets.
+// Only this warp touches lam and the bitmaps while it runs, so it uses plain
+// loads and stores (L1-cached when CACHED) and no atomics on global memory:
+// concurrent updates of one point or one bitmap word inside a 32-lane chunk
+// are combined with __match_any_sync / __reduce_*_sync first.
+constexpr int32_t LAM_F = -1, LAM_C = -2;
+constexpr int8_t CF_F = 0, CF_C = 1;   // values of the cf marker
 
 struct RSArgs {
     int64_t n;
     const int64_t *srp, *strp;
     const int32_t *sci, *stci;
     int32_t *lam;
-    int8_t *state;
+    int8_t *cf;
     uint64_t *L0, *L1, *L2;
     int64_t w0, w1, w2;
     int nb;            // buckets 0 .. nb-1 (bucket 0 unused)
     int top;           // largest bucket that may be non-empty
+    int max_st, touch_cap;
     int64_t cap;       // bound on search iterations
     int *err;
 };
-
-__device__ __forceinline__ void rs_insert(const RSArgs &a, uint64_t *L2, int b, int64_t k) {
-    uint64_t m0 = 1ull << (k & 63);
-    uint64_t o0 = atomicOr((unsigned long long *)&a.L0[(int64_t)b * a.w0 + (k >> 6)], (unsigned long long)m0);
-    if (o0 == 0) {
-        int64_t i1 = k >> 6;
-        uint64_t o1 = atomicOr((unsigned long long *)&a.L1[(int64_t)b * a.w1 + (i1 >> 6)],
-                               (unsigned long long)(1ull << (i1 & 63)));
-        if (o1 == 0) {
-            int64_t i2 = i1 >> 6;
-            atomicOr((unsigned long long *)&L2[(int64_t)b * a.w2 + (i2 >> 6)], (unsigned long long)(1ull << (i2 & 63)));
-        }
-    }
-}
 
 __global__ void rs_init_kernel(RSArgs a) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
         int32_t lam = (int32_t)(a.strp[i + 1] - a.strp[i]);
         bool isolated = (a.srp[i + 1] == a.srp[i]) && lam == 0;
-        a.lam[i] = lam;
-        a.state[i] = isolated ? ST_F : ST_U;
-        if (!isolated && lam > 0) rs_insert(a, a.L2, lam, i);
+        a.lam[i] = isolated ? LAM_F : lam;
+        if (!isolated && lam > 0) {
+            uint64_t o0 = atomicOr((unsigned long long *)&a.L0[(int64_t)lam * a.w0 + (i >> 6)],
+                                   (unsigned long long)(1ull << (i & 63)));
+            if (o0 == 0) {
+                int64_t i1 = i >> 6;
+                uint64_t o1 = atomicOr((unsigned long long *)&a.L1[(int64_t)lam * a.w1 + (i1 >> 6)],
+                                       (unsigned long long)(1ull << (i1 & 63)));
+                if (o1 == 0) {
+                    int64_t i2 = i1 >> 6;
+                    atomicOr((unsigned long long *)&a.L2[(int64_t)lam * a.w2 + (i2 >> 6)],
+                             (unsigned long long)(1ull << (i2 & 63)));
+                }
+            }
+        }
     }
 }
 
-// Warp 0 finds the undecided point of largest measure (ties -> smallest
-// index).  Returns the point, -1 when the largest measure is 0, -2 when the
-// iteration cap is hit.
+template <bool CACHED, typename T>
+__device__ __forceinline__ T rs_ld(const T *p) {
+    if (CACHED) return *p;
+    return __ldcg(p);
+}
+
+// Lane 0 walks level 1 and level 0 of bucket b after the warp found a
+// non-empty level-2 word.  Returns the point or -3 (retry after clearing a
+// stale bit).
+template <bool CACHED>
+__device__ int64_t rs_probe(const RSArgs &a, uint64_t *L2s, int b, int64_t w) {
+    uint64_t *p2 = &L2s[(int64_t)b * a.w2 + w];
+    uint64_t l2 = *p2;
+    int bit2 = __ffsll((long long)l2) - 1;
+    int64_t i1 = w * 64 + bit2;
+    uint64_t *p1 = &a.L1[(int64_t)b * a.w1 + i1];
+    uint64_t l1 = rs_ld<CACHED>((const unsigned long long *)p1);
+    if (l1 == 0ull) {
+        *p2 = l2 & ~(1ull << bit2);
+        return -3;
+    }
+    int bit1 = __ffsll((long long)l1) - 1;
+    int64_t i0 = i1 * 64 + bit1;
+    uint64_t *p0 = &a.L0[(int64_t)b * a.w0 + i0];
+    uint64_t l0 = rs_ld<CACHED>((const unsigned long long *)p0);
+    bool clear0 = false;
+    if (l0 == 0ull) {
+        clear0 = true;
+    } else {
+        int bit0 = __ffsll((long long)l0) - 1;
+        int64_t k = i0 * 64 + bit0;
+        if (rs_ld<CACHED>(&a.lam[k]) == b) return k;
+        uint64_t n0 = l0 & ~(1ull << bit0);
+        *p0 = n0;
+        clear0 = (n0 == 0ull);
+    }
+    if (clear0) {
+        uint64_t n1 = l1 & ~(1ull << bit1);
+        *p1 = n1;
+        if (n1 == 0ull) *p2 = l2 & ~(1ull << bit2);
+    }
+    return -3;
+}
+
+// The undecided point of largest measure (ties -> smallest index); -1 when
+// the largest measure is 0, -2 when the iteration cap is hit.
+template <bool CACHED>
 __device__ int64_t rs_search(const RSArgs &a, uint64_t *L2s, int *top, int64_t *iters) {
     int lane = threadIdx.x & 31;
     int b = *top;
@@ -183,128 +230,379 @@ __device__ int64_t rs_search(const RSArgs &a, uint64_t *L2s, int *top, int64_t *
             if (bal) { w = base + __ffs(bal) - 1; break; }
         }
         if (w < 0) { --b; continue; }
-        int64_t res = -3;   // retry
-        if (lane == 0) {
-            uint64_t *p2 = &L2s[(int64_t)b * a.w2 + w];
-            uint64_t l2 = *p2;
-            int bit2 = __ffsll((long long)l2) - 1;
-            int64_t i1 = w * 64 + bit2;
-            uint64_t *p1 = &a.L1[(int64_t)b * a.w1 + i1];
-            uint64_t l1 = __ldcg((const unsigned long long *)p1);
-            if (l1 == 0ull) {
-                *p2 = l2 & ~(1ull << bit2);
-            } else {
-                int bit1 = __ffsll((long long)l1) - 1;
-                int64_t i0 = i1 * 64 + bit1;
-                uint64_t *p0 = &a.L0[(int64_t)b * a.w0 + i0];
-                uint64_t l0 = __ldcg((const unsigned long long *)p0);
-                bool clear0 = false;
-                if (l0 == 0ull) {
-                    clear0 = true;
-                } else {
-                    int bit0 = __ffsll((long long)l0) - 1;
-                    int64_t k = i0 * 64 + bit0;
-                    if (__ldcg(&a.state[k]) == ST_U && __ldcg(&a.lam[k]) == b) {
-                        res = k;
-                    } else {
-                        uint64_t n0 = l0 & ~(1ull << bit0);
-                        *p0 = n0;
-                        clear0 = (n0 == 0ull);
-                    }
+        int64_t res = -3;
+        if (lane == 0) res = rs_probe<CACHED>(a, L2s, b, w);
+        res = __shfl_sync(FULL, res, 0);
+        __syncwarp();
+        if (res >= 0) { *top = b; return res; }
+    }
+}
+
+// Add dlt to the measure of every still undecided point k given by the
+// active lanes (duplicates within the chunk are combined), recording the
+// points it changed in touched[].
+template <bool CACHED>
+__device__ __forceinline__ void rs_bump(const RSArgs &a, int32_t k, bool active, int dlt, int32_t *touched,
+                                        int &nt) {
+    int lane = threadIdx.x & 31;
+    unsigned m = __match_any_sync(FULL, active ? k : -1);
+    bool leader = active && (__ffs(m) - 1) == lane;
+    bool changed = false;
+    if (leader) {
+        int32_t v = rs_ld<CACHED>(&a.lam[k]);
+        if (v >= 0) {
+            a.lam[k] = v + dlt * __popc(m);
+            changed = true;
+        }
+    }
+    unsigned bal = __ballot_sync(FULL, changed);
+    if (changed) {
+        int p = nt + __popc(bal & lanemask_lt());
+        if (p < a.touch_cap) touched[p] = k;
+    }
+    nt += __popc(bal);
+}
+
+template <bool CACHED>
+__global__ void __launch_bounds__(32) rs_warp_kernel(RSArgs a) {
+    extern __shared__ uint64_t smem[];
+    uint64_t *L2s = smem;                                            // nb * w2 words
+    int32_t *newF = (int32_t *)(smem + (int64_t)a.nb * a.w2);        // max_st
+    int32_t *touched = newF + a.max_st + 1;                          // touch_cap
+    int lane = threadIdx.x & 31;
+    for (int64_t t = lane; t < (int64_t)a.nb * a.w2; t += 32) L2s[t] = a.L2[t];
+    int top = a.top;
+    int64_t iters = 0;
+    __syncwarp();
+    for (int64_t pick_no = 0; pick_no <= a.n; ++pick_no) {
+        int64_t i = rs_search<CACHED>(a, L2s, &top, &iters);
+        if (i < 0) {
+            if (i == -2 && lane == 0) atomicOr(a.err, AIR_DEVERR_RS_CAP);
+            break;
+        }
+        if (lane == 0) a.lam[i] = LAM_C;
+        __syncwarp();
+        // undecided strong dependants of i become F
+        int nf = 0;
+        int64_t qb = a.strp[i], qe = a.strp[i + 1];
+        for (int64_t q0 = qb; q0 < qe; q0 += 32) {
+            int64_t q = q0 + lane;
+            int32_t j = q < qe ? a.stci[q] : -1;
+            bool u = j >= 0 && rs_ld<CACHED>(&a.lam[j]) >= 0;
+            if (u) a.lam[j] = LAM_F;
+            unsigned bal = __ballot_sync(FULL, u);
+            if (u) newF[nf + __popc(bal & lanemask_lt())] = j;
+            nf += __popc(bal);
+        }
+        __syncwarp();
+        // measure updates: +1 on S_j of each new F point, -1 on S_i
+        int nt = 0;
+        for (int f = 0; f < nf; ++f) {
+            int32_t j = newF[f];
+            int64_t sb = a.srp[j], se = a.srp[j + 1];
+            for (int64_t q0 = sb; q0 < se; q0 += 32) {
+                int64_t q = q0 + lane;
+                bool act = q < se;
+                int32_t k = act ? a.sci[q] : -1;
+                rs_bump<CACHED>(a, k, act, +1, touched, nt);
+                __syncwarp();
+            }
+        }
+        {
+            int64_t sb = a.srp[i], se = a.srp[i + 1];
+            for (int64_t q0 = sb; q0 < se; q0 += 32) {
+                int64_t q = q0 + lane;
+                bool act = q < se;
+                int32_t k = act ? a.sci[q] : -1;
+                rs_bump<CACHED>(a, k, act, -1, touched, nt);
+                __syncwarp();
+            }
+        }
+        if (nt > a.touch_cap) {       // cannot happen with the host-side bound; fail loudly
+            if (lane == 0) atomicOr(a.err, AIR_DEVERR_RS_CAP);
+            break;
+        }
+        // re-insert every touched point under its final measure
+        for (int t0 = 0; t0 < nt; t0 += 32) {
+            int t = t0 + lane;
+            int32_t k = t < nt ? touched[t] : -1;
+            int32_t v = k >= 0 ? rs_ld<CACHED>(&a.lam[k]) : -1;
+            bool ins = v > 0;
+            unsigned long long key0 = ins ? (unsigned long long)v * (unsigned long long)a.w0 + (unsigned long long)(k >> 6)
+                                          : ~0ull;
+            unsigned m0 = __match_any_sync(FULL, key0);
+            unsigned long long bit0 = ins ? (1ull << (k & 63)) : 0ull;
+            unsigned lo = __reduce_or_sync(m0, (unsigned)bit0);
+            unsigned hi = __reduce_or_sync(m0, (unsigned)(bit0 >> 32));
+            bool lead0 = ins && (__ffs(m0) - 1) == lane;
+            bool need1 = false;
+            if (lead0) {
+                uint64_t old = rs_ld<CACHED>((const unsigned long long *)&a.L0[key0]);
+                a.L0[key0] = old | ((uint64_t)hi << 32) | lo;
+                need1 = (old == 0ull);
+            }
+            int64_t i1 = k >> 6;
+            unsigned long long key1 = need1 ? (unsigned long long)v * (unsigned long long)a.w1 + (unsigned long long)(i1 >> 6)
+                                            : ~0ull;
+            unsigned m1 = __match_any_sync(FULL, key1);
+            unsigned long long bit1 = need1 ? (1ull << (i1 & 63)) : 0ull;
+            unsigned lo1 = __reduce_or_sync(m1, (unsigned)bit1);
+            unsigned hi1 = __reduce_or_sync(m1, (unsigned)(bit1 >> 32));
+            bool lead1 = need1 && (__ffs(m1) - 1) == lane;
+            if (lead1) {
+                uint64_t old = rs_ld<CACHED>((const unsigned long long *)&a.L1[key1]);
+                a.L1[key1] = old | ((uint64_t)hi1 << 32) | lo1;
+                if (old == 0ull) {
+                    int64_t i2 = i1 >> 6;
+                    atomicOr((unsigned long long *)&L2s[(int64_t)v * a.w2 + (i2 >> 6)],
+                             (unsigned long long)(1ull << (i2 & 63)));
                 }
-                if (clear0) {
-                    uint64_t n1 = l1 & ~(1ull << bit1);
-                    *p1 = n1;
-                    if (n1 == 0ull) *p2 = l2 & ~(1ull << bit2);
+            }
+            int vmax = ins ? v : 0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) vmax = max(vmax, __shfl_xor_sync(FULL, vmax, o));
+            if (vmax > top) top = vmax;
+            __syncwarp();
+        }
+    }
+}
+
+__global__ void rs_finish_kernel(int64_t n, const int32_t *lam, int8_t *cf) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        cf[i] = lam[i] == LAM_C ? 1 : 0;
+}
+
+// ---------------------------------------- first pass, exact-bitmap version
+// The same sequential first pass, with three changes that shorten the chain
+// of dependent memory accesses per pick:
+//  * the bucket bitmaps are kept exact (a point is removed from its old
+//    bucket whenever its measure or state changes), so the search needs no
+//    validation load and never meets stale bits;
+//  * for every point i the lists S^T_i, S_j (j in S^T_i, in order) and S_i
+//    are gathered once into one contiguous array of (point, tag) entries, so
+//    a pick reads its whole two-hop neighbourhood in one coalesced access;
+//  * measures and states are int8 (measure <= 2 max|S^T| <= 124, -1 = F,
+//    -2 = C), which keeps the state of ~10^7 points resident in L2.
+constexpr uint32_t TAG_J = 0xffffffffu, TAG_SI = 0xfffffffeu;
+constexpr int8_t L8_F = -1, L8_C = -2;
+
+struct RS3Args {
+    int64_t n;
+    const int64_t *srp, *strp, *hop_ptr;
+    const int32_t *sci, *stci;
+    const unsigned long long *hop;
+    int8_t *lam;
+    int8_t *cf;
+    uint64_t *L0, *L1, *L2;
+    int64_t w0, w1, w2;
+    int nb, top, max_st;
+    int64_t cap;
+    int *err;
+};
+
+__global__ void hop_count_kernel(int64_t n, const int64_t *srp, const int64_t *strp, const int32_t *stci,
+                                 int32_t *cnt) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t c = (strp[i + 1] - strp[i]) + (srp[i + 1] - srp[i]);
+        for (int64_t q = strp[i]; q < strp[i + 1]; ++q) {
+            int32_t j = stci[q];
+            c += srp[j + 1] - srp[j];
+        }
+        cnt[i] = (int32_t)c;
+    }
+}
+
+__global__ void hop_fill_kernel(int64_t n, const int64_t *srp, const int32_t *sci, const int64_t *strp,
+                                const int32_t *stci, const int64_t *hop_ptr, unsigned long long *hop) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t p = hop_ptr[i];
+        for (int64_t q = strp[i]; q < strp[i + 1]; ++q)
+            hop[p++] = ((unsigned long long)TAG_J << 32) | (unsigned)stci[q];
+        uint32_t t = 0;
+        for (int64_t q = strp[i]; q < strp[i + 1]; ++q, ++t) {
+            int32_t j = stci[q];
+            for (int64_t r = srp[j]; r < srp[j + 1]; ++r) hop[p++] = ((unsigned long long)t << 32) | (unsigned)sci[r];
+        }
+        for (int64_t r = srp[i]; r < srp[i + 1]; ++r) hop[p++] = ((unsigned long long)TAG_SI << 32) | (unsigned)sci[r];
+    }
+}
+
+__global__ void rs3_init_kernel(RS3Args a) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t lam = (int32_t)(a.strp[i + 1] - a.strp[i]);
+        bool isolated = (a.srp[i + 1] == a.srp[i]) && lam == 0;
+        a.lam[i] = isolated ? L8_F : (int8_t)lam;
+        if (!isolated && lam > 0) {
+            uint64_t o0 = atomicOr((unsigned long long *)&a.L0[(int64_t)lam * a.w0 + (i >> 6)],
+                                   (unsigned long long)(1ull << (i & 63)));
+            if (o0 == 0) {
+                int64_t i1 = i >> 6;
+                uint64_t o1 = atomicOr((unsigned long long *)&a.L1[(int64_t)lam * a.w1 + (i1 >> 6)],
+                                       (unsigned long long)(1ull << (i1 & 63)));
+                if (o1 == 0) {
+                    int64_t i2 = i1 >> 6;
+                    atomicOr((unsigned long long *)&a.L2[(int64_t)lam * a.w2 + (i2 >> 6)],
+                             (unsigned long long)(1ull << (i2 & 63)));
                 }
             }
         }
+    }
+}
+
+__device__ __forceinline__ unsigned long long warp_or_u64(unsigned m, unsigned long long v) {
+    unsigned lo = __reduce_or_sync(m, (unsigned)v);
+    unsigned hi = __reduce_or_sync(m, (unsigned)(v >> 32));
+    return ((unsigned long long)hi << 32) | lo;
+}
+
+// Set (set = true) or clear point k in bucket b for every valid lane; the
+// whole warp calls it.  Lanes hitting the same 64-bit word are combined, and
+// the level-1 / level-2 summaries follow every word that becomes empty or
+// non-empty.
+__device__ __forceinline__ void bm_update(const RS3Args &a, uint64_t *L2s, int b, int64_t k, bool valid, bool set) {
+    if (!__any_sync(FULL, valid)) return;
+    int lane = threadIdx.x & 31;
+    unsigned long long key0 = valid ? (unsigned long long)b * (unsigned long long)a.w0 + (unsigned long long)(k >> 6)
+                                    : ~0ull;
+    unsigned m0 = __match_any_sync(FULL, key0);
+    unsigned long long comb = warp_or_u64(m0, valid ? (1ull << (k & 63)) : 0ull);
+    bool lead = valid && (__ffs(m0) - 1) == lane;
+    bool t1 = false;
+    if (lead) {
+        uint64_t old = a.L0[key0];
+        uint64_t nw = set ? (old | comb) : (old & ~comb);
+        a.L0[key0] = nw;
+        t1 = (old == 0ull) != (nw == 0ull);
+    }
+    if (__any_sync(FULL, t1)) {
+        int64_t i1 = k >> 6;
+        unsigned long long key1 = t1 ? (unsigned long long)b * (unsigned long long)a.w1 + (unsigned long long)(i1 >> 6)
+                                     : ~0ull;
+        unsigned m1 = __match_any_sync(FULL, key1);
+        unsigned long long comb1 = warp_or_u64(m1, t1 ? (1ull << (i1 & 63)) : 0ull);
+        bool lead1 = t1 && (__ffs(m1) - 1) == lane;
+        if (lead1) {
+            uint64_t old1 = a.L1[key1];
+            uint64_t nw1 = set ? (old1 | comb1) : (old1 & ~comb1);
+            a.L1[key1] = nw1;
+            if ((old1 == 0ull) != (nw1 == 0ull)) {
+                int64_t i2 = i1 >> 6;
+                unsigned long long *p2 = (unsigned long long *)&L2s[(int64_t)b * a.w2 + (i2 >> 6)];
+                unsigned long long bit2 = 1ull << (i2 & 63);
+                if (set) atomicOr(p2, bit2); else atomicAnd(p2, ~bit2);
+            }
+        }
+    }
+    __syncwarp();
+}
+
+// Largest measure, smallest index: -1 when the largest measure is 0, -2 on
+// the iteration cap or an inconsistent bitmap.
+__device__ int64_t rs3_search(const RS3Args &a, uint64_t *L2s, int *top, int64_t *iters) {
+    int lane = threadIdx.x & 31;
+    int b = *top;
+    while (true) {
+        if (b < 1) { *top = 0; return -1; }
+        if (++(*iters) > a.cap) return -2;
+        int64_t w = -1;
+        for (int64_t base = 0; base < a.w2; base += 32) {
+            uint64_t val = (base + lane < a.w2) ? L2s[(int64_t)b * a.w2 + base + lane] : 0ull;
+            unsigned bal = __ballot_sync(FULL, val != 0ull);
+            if (bal) { w = base + __ffs(bal) - 1; break; }
+        }
+        if (w < 0) { --b; continue; }
+        int64_t res = -2;
+        if (lane == 0) {
+            uint64_t l2 = L2s[(int64_t)b * a.w2 + w];
+            int64_t i1 = w * 64 + (__ffsll((long long)l2) - 1);
+            uint64_t l1 = a.L1[(int64_t)b * a.w1 + i1];
+            if (l1 != 0ull) {
+                int64_t i0 = i1 * 64 + (__ffsll((long long)l1) - 1);
+                uint64_t l0 = a.L0[(int64_t)b * a.w0 + i0];
+                if (l0 != 0ull) res = i0 * 64 + (__ffsll((long long)l0) - 1);
+            }
+        }
         res = __shfl_sync(FULL, res, 0);
-        if (res >= 0) { *top = b; return res; }
+        *top = b;
+        return res;
+    }
+}
+
+__global__ void __launch_bounds__(32) rs3_warp_kernel(RS3Args a) {
+    extern __shared__ uint64_t smem[];
+    uint64_t *L2s = smem;                                              // nb * w2 words
+    int8_t *jflag = (int8_t *)(smem + (int64_t)a.nb * a.w2);          // max_st + 1
+    int lane = threadIdx.x & 31;
+    for (int64_t t = lane; t < (int64_t)a.nb * a.w2; t += 32) L2s[t] = a.L2[t];
+    int top = a.top;
+    int64_t iters = 0;
+    __syncwarp();
+    for (int64_t pick_no = 0; pick_no <= a.n; ++pick_no) {
+        int64_t i = rs3_search(a, L2s, &top, &iters);
+        if (i < 0) {
+            if (i == -2 && lane == 0) atomicOr(a.err, AIR_DEVERR_RS_CAP);
+            break;
+        }
+        int b = top;
+        bm_update(a, L2s, b, i, lane == 0, false);
+        if (lane == 0) a.lam[i] = L8_C;
+        int64_t h0 = a.hop_ptr[i], h1 = a.hop_ptr[i + 1];
+        int64_t c = a.strp[i + 1] - a.strp[i];
+        __syncwarp();
+        // undecided strong dependants of i become F
+        for (int64_t e0 = h0; e0 < h0 + c; e0 += 32) {
+            int64_t e = e0 + lane;
+            bool act = e < h0 + c;
+            int32_t j = act ? (int32_t)(unsigned)a.hop[e] : 0;
+            int old = act ? (int)a.lam[j] : -3;
+            bool u = old >= 0;
+            if (u) a.lam[j] = L8_F;
+            if (act) jflag[e - h0] = u ? 1 : 0;
+            bm_update(a, L2s, old, j, u && old >= 1, false);
+        }
+        // +1 on S_j of each new F point j, -1 on S_i
+        int vmax = 0;
+        for (int64_t e0 = h0 + c; e0 < h1; e0 += 32) {
+            int64_t e = e0 + lane;
+            bool act = e < h1;
+            unsigned long long ent = act ? a.hop[e] : 0ull;
+            int32_t k = (int32_t)(unsigned)ent;
+            uint32_t tag = (uint32_t)(ent >> 32);
+            int dlt = 0;
+            if (act) dlt = (tag == TAG_SI) ? -1 : (jflag[tag] ? 1 : 0);
+            int cur = dlt != 0 ? (int)a.lam[k] : -3;
+            bool live = dlt != 0 && cur >= 0;
+            unsigned m = __match_any_sync(FULL, live ? k : -1);
+            int sum = __reduce_add_sync(m, live ? dlt : 0);
+            bool lead = live && (__ffs(m) - 1) == lane;
+            int nv = cur + sum;
+            bool mv = lead && nv != cur;
+            if (lead) a.lam[k] = (int8_t)nv;
+            bm_update(a, L2s, cur, k, mv && cur >= 1, false);
+            bm_update(a, L2s, nv, k, mv && nv >= 1, true);
+            if (mv && nv > vmax) vmax = nv;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) vmax = max(vmax, __shfl_xor_sync(FULL, vmax, o));
+        if (vmax > top) top = vmax;
         __syncwarp();
     }
 }
 
-__global__ void __launch_bounds__(RS_THREADS) rs_main_kernel(RSArgs a) {
-    extern __shared__ uint64_t smem[];
-    uint64_t *L2s = smem;                                  // nb * w2 words
-    int32_t *newF = (int32_t *)(smem + (int64_t)a.nb * a.w2);
-    __shared__ int s_top, s_nf;
-    __shared__ long long s_pick;
-    int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
-    for (int64_t t = tid; t < (int64_t)a.nb * a.w2; t += blockDim.x) L2s[t] = a.L2[t];
-    if (tid == 0) s_top = a.top;
-    int64_t iters = 0;
-    __syncthreads();
-    for (int64_t pick_no = 0; pick_no <= a.n; ++pick_no) {
-        if (warp == 0) {
-            int top = s_top;
-            int64_t p = rs_search(a, L2s, &top, &iters);
-            if (lane == 0) { s_pick = p; s_top = top; s_nf = 0; if (p >= 0) a.state[p] = ST_C; }
-        }
-        __syncthreads();
-        int64_t i = s_pick;
-        if (i < 0) {
-            if (i == -2 && tid == 0) atomicOr(a.err, AIR_DEVERR_RS_CAP);
-            break;
-        }
-        // undecided strong dependants of i become F
-        for (int64_t q = a.strp[i] + tid; q < a.strp[i + 1]; q += blockDim.x) {
-            int32_t j = a.stci[q];
-            if (__ldcg(&a.state[j]) == ST_U) {
-                a.state[j] = ST_F;
-                newF[atomicAdd(&s_nf, 1)] = j;
-            }
-        }
-        __syncthreads();
-        int nf = s_nf;
-        // measure updates: +1 on S_j of every new F point j, -1 on S_i
-        for (int f = warp; f < nf; f += nwarps) {
-            int32_t j = newF[f];
-            for (int64_t q = a.srp[j] + lane; q < a.srp[j + 1]; q += 32) {
-                int32_t k = a.sci[q];
-                if (__ldcg(&a.state[k]) == ST_U) atomicAdd(&a.lam[k], 1);
-            }
-        }
-        for (int64_t q = a.srp[i] + tid; q < a.srp[i + 1]; q += blockDim.x) {
-            int32_t k = a.sci[q];
-            if (__ldcg(&a.state[k]) == ST_U) atomicSub(&a.lam[k], 1);
-        }
-        __syncthreads();
-        // re-insert every touched undecided point under its new measure
-        for (int f = warp; f < nf; f += nwarps) {
-            int32_t j = newF[f];
-            for (int64_t q = a.srp[j] + lane; q < a.srp[j + 1]; q += 32) {
-                int32_t k = a.sci[q];
-                if (__ldcg(&a.state[k]) == ST_U) {
-                    int32_t l = __ldcg(&a.lam[k]);
-                    if (l > 0) { rs_insert(a, L2s, l, k); atomicMax(&s_top, l); }
-                }
-            }
-        }
-        for (int64_t q = a.srp[i] + tid; q < a.srp[i + 1]; q += blockDim.x) {
-            int32_t k = a.sci[q];
-            if (__ldcg(&a.state[k]) == ST_U) {
-                int32_t l = __ldcg(&a.lam[k]);
-                if (l > 0) { rs_insert(a, L2s, l, k); atomicMax(&s_top, l); }
-            }
-        }
-        __syncthreads();
-    }
-    __syncthreads();
-    for (int64_t k = tid; k < a.n; k += blockDim.x)
-        if (__ldcg(&a.state[k]) == ST_U) a.state[k] = ST_F;
+__global__ void rs3_finish_kernel(int64_t n, const int8_t *lam, int8_t *cf) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        cf[i] = lam[i] == L8_C ? 1 : 0;
 }
 
 // -------------------------------------------------------------- coarse ids
 __global__ void cflag_kernel(int64_t n, const int8_t *cf, int32_t *flag) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        flag[i] = cf[i] == ST_C ? 1 : 0;
+        flag[i] = cf[i] == 1 ? 1 : 0;
 }
 
 __global__ void cid_kernel(int64_t n, const int8_t *cf, const int64_t *scan, int32_t *cid, int32_t *crows) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        if (cf[i] == ST_C) {
+        if (cf[i] == 1) {
             cid[i] = (int32_t)scan[i];
             crows[scan[i]] = (int32_t)i;
         } else {
@@ -320,7 +618,7 @@ __global__ void lair_count_kernel(int64_t nc, const int32_t *crows, const int64_
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nc; t += (int64_t)gridDim.x * blockDim.x) {
         int32_t i = crows[t];
         int c = 0;
-        for (int64_t q = srp[i]; q < srp[i + 1]; ++q) c += cf[sci[q]] == ST_F;
+        for (int64_t q = srp[i]; q < srp[i + 1]; ++q) c += cf[sci[q]] == CF_F;
         cnt[t] = c + 1;
     }
 }
@@ -357,7 +655,7 @@ __global__ void lair_solve_kernel(int64_t nc, const int32_t *crows, const int64_
         for (int64_t q0 = srp[i]; q0 < srp[i + 1]; q0 += 32) {
             int64_t q = q0 + lane;
             int32_t j = q < srp[i + 1] ? sci[q] : -1;
-            bool f = j >= 0 && cf[j] == ST_F;
+            bool f = j >= 0 && cf[j] == CF_F;
             unsigned bal = __ballot_sync(FULL, f);
             if (f) N[m + __popc(bal & lanemask_lt())] = j;
             m += __popc(bal);
@@ -461,7 +759,7 @@ __global__ void onepoint_kernel(int64_t n, const int64_t *rp, const int32_t *ci,
                                 const int8_t *cf, const int32_t *cid, int32_t *pcol) {
     int lane = threadIdx.x & 31;
     for (int64_t i = global_warp(); i < n; i += warp_count()) {
-        if (cf[i] == ST_C) {
+        if (cf[i] == CF_C) {
             if (lane == 0) pcol[i] = cid[i];
             continue;
         }
@@ -477,7 +775,7 @@ __global__ void onepoint_kernel(int64_t n, const int64_t *rp, const int32_t *ci,
             for (int64_t k = b + lane; k < e; k += 32) {
                 int32_t c = ci[k];
                 double a = fabs(v[k]);
-                if (c != i && a >= thr && cf[c] == ST_C && a > bv) { bv = a; best = c; }
+                if (c != i && a >= thr && cf[c] == CF_C && a > bv) { bv = a; best = c; }
             }
         }
 #pragma unroll
@@ -706,11 +1004,72 @@ int air_transpose_pattern(int64_t n, int64_t nnz, const int64_t *srp, const int3
     return AIR_OK;
 }
 
+static int rs_first_pass_v3(int64_t n, const int64_t *srp, const int32_t *sci, const int64_t *strp,
+                            const int32_t *stci, int32_t max_st, int8_t *cf, int *d_err, cudaStream_t s) {
+    RS3Args a;
+    a.n = n; a.srp = srp; a.sci = sci; a.strp = strp; a.stci = stci;
+    a.cf = cf;
+    a.nb = 2 * max_st + 1;
+    if (a.nb < 2) a.nb = 2;
+    a.top = a.nb - 1;
+    a.max_st = max_st;
+    a.w0 = (n + 63) / 64;
+    a.w1 = (a.w0 + 63) / 64;
+    a.w2 = (a.w1 + 63) / 64;
+    a.err = d_err;
+    // each pick raises the top bucket by < nb, so the search loop runs at most
+    // (n + 1) (nb + 1) times
+    a.cap = (n + 1) * (int64_t)(a.nb + 1) + 4096;
+    // two-hop lists
+    int32_t *cnt = nullptr;
+    int64_t *hop_ptr = nullptr;
+    AIR_CUDA(cudaMallocAsync(&cnt, (size_t)(n > 0 ? n : 1) * sizeof(int32_t), s));
+    AIR_CUDA(cudaMallocAsync(&hop_ptr, (size_t)(n + 1) * sizeof(int64_t), s));
+    hop_count_kernel<<<air_counted(grid_for(n, 256)), 256, 0, s>>>(n, srp, strp, stci, cnt);
+    AIR_LAUNCH();
+    AIR_TRY(air_exclusive_scan_i32(cnt, hop_ptr, n, s));
+    int64_t nhop = 0;
+    AIR_CUDA(cudaMemcpyAsync(&nhop, hop_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    AIR_CUDA(cudaStreamSynchronize(s));
+    unsigned long long *hop = nullptr;
+    AIR_CUDA(cudaMallocAsync(&hop, (size_t)(nhop > 0 ? nhop : 1) * sizeof(unsigned long long), s));
+    hop_fill_kernel<<<air_counted(grid_for(n, 256)), 256, 0, s>>>(n, srp, sci, strp, stci, hop_ptr, hop);
+    AIR_LAUNCH();
+    a.hop_ptr = hop_ptr;
+    a.hop = hop;
+    size_t words = (size_t)a.nb * (size_t)(a.w0 + a.w1 + a.w2);
+    uint64_t *bits = nullptr;
+    int8_t *lam = nullptr;
+    AIR_CUDA(cudaMallocAsync(&bits, words * sizeof(uint64_t), s));
+    AIR_CUDA(cudaMallocAsync(&lam, (size_t)(n > 0 ? n : 1), s));
+    AIR_CUDA(cudaMemsetAsync(bits, 0, words * sizeof(uint64_t), s));
+    a.L0 = bits;
+    a.L1 = bits + (size_t)a.nb * a.w0;
+    a.L2 = a.L1 + (size_t)a.nb * a.w1;
+    a.lam = lam;
+    rs3_init_kernel<<<air_counted(grid_for(n, 256)), 256, 0, s>>>(a);
+    AIR_LAUNCH();
+    size_t smem = (size_t)a.nb * a.w2 * sizeof(uint64_t) + (size_t)(max_st + 8);
+    AIR_CUDA(cudaFuncSetAttribute(rs3_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    rs3_warp_kernel<<<air_counted(1), 32, smem, s>>>(a);
+    AIR_LAUNCH();
+    rs3_finish_kernel<<<air_counted(grid_for(n, 256)), 256, 0, s>>>(n, lam, cf);
+    AIR_LAUNCH();
+    cudaFreeAsync(bits, s);
+    cudaFreeAsync(lam, s);
+    cudaFreeAsync(hop, s);
+    cudaFreeAsync(hop_ptr, s);
+    cudaFreeAsync(cnt, s);
+    return AIR_OK;
+}
+
 int air_rs_first_pass(int64_t n, const int64_t *srp, const int32_t *sci, const int64_t *strp, const int32_t *stci,
-                      int32_t max_st, int8_t *cf, int *d_err, cudaStream_t s) {
+                      int32_t max_st, int32_t max_s, int8_t *cf, int *d_err, int cached, cudaStream_t s) {
+    if (cached == 2 && 2 * max_st + 1 <= 125)
+        return rs_first_pass_v3(n, srp, sci, strp, stci, max_st, cf, d_err, s);
     RSArgs a;
     a.n = n; a.srp = srp; a.sci = sci; a.strp = strp; a.stci = stci;
-    a.state = cf;
+    a.cf = cf;
     a.nb = 2 * max_st + 1;
     if (a.nb < 2) a.nb = 2;
     a.top = a.nb - 1;
@@ -718,6 +1077,9 @@ int air_rs_first_pass(int64_t n, const int64_t *srp, const int32_t *sci, const i
     a.w1 = (a.w0 + 63) / 64;
     a.w2 = (a.w1 + 63) / 64;
     a.err = d_err;
+    a.max_st = max_st;
+    // touched points per pick: S_j of every new F point j plus S_i
+    a.touch_cap = (max_st + 1) * (max_s > 0 ? max_s : 1) + 64;
     int64_t nnz_s = 0;
     AIR_CUDA(cudaMemcpyAsync(&nnz_s, srp + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     AIR_CUDA(cudaStreamSynchronize(s));
@@ -734,9 +1096,17 @@ int air_rs_first_pass(int64_t n, const int64_t *srp, const int32_t *sci, const i
     a.lam = lam;
     rs_init_kernel<<<air_counted(grid_for(n, 256)), 256, 0, s>>>(a);
     AIR_LAUNCH();
-    size_t smem = (size_t)a.nb * a.w2 * sizeof(uint64_t) + (size_t)(max_st + 1) * sizeof(int32_t);
-    AIR_CUDA(cudaFuncSetAttribute(rs_main_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    rs_main_kernel<<<air_counted(1), RS_THREADS, smem, s>>>(a);
+    size_t smem = (size_t)a.nb * a.w2 * sizeof(uint64_t) + (size_t)(max_st + 1 + a.touch_cap) * sizeof(int32_t);
+    if (smem > 200 * 1024) return AIR_ERR_UNSUPPORTED;
+    if (cached) {
+        AIR_CUDA(cudaFuncSetAttribute(rs_warp_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        rs_warp_kernel<true><<<air_counted(1), 32, smem, s>>>(a);
+    } else {
+        AIR_CUDA(cudaFuncSetAttribute(rs_warp_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        rs_warp_kernel<false><<<air_counted(1), 32, smem, s>>>(a);
+    }
+    AIR_LAUNCH();
+    rs_finish_kernel<<<air_counted(grid_for(n, 256)), 256, 0, s>>>(n, lam, cf);
     AIR_LAUNCH();
     cudaFreeAsync(bits, s);
     cudaFreeAsync(lam, s);
