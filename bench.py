@@ -283,8 +283,20 @@ def run_ours(args):
     # V-cycle and SpMV roofline (FP32 hierarchy is the reported form)
     gbs_peak, peak_kind = peaks()
     rl = {}
+    breakdown = {}
     for prec, key in ((1, "f32"), (0, "f64")):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
         H = air.setup(A, theta=0.25, distance=1, precision=prec)
+        t_setup = time.perf_counter() - t0
+        xs = torch.empty_like(b)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, inf_s = air.gmres_solve(A, H, b, xs, rtol=args.rtol)
+        torch.cuda.synchronize()
+        t_solve = time.perf_counter() - t0
+        breakdown[key] = {"setup_s": t_setup, "solve_s": t_solve, "iters": inf_s.iters,
+                          "setup_phase_ms": H.setup_timings(), "levels": H.levels()}
         vb = vcycle_bytes(H, 4 if prec == 1 else 8)
         xv = torch.empty_like(b)
         for _ in range(3):
@@ -353,6 +365,7 @@ def run_ours(args):
         "roofline_spmv": {"bound": "hbm", "kernel": "spmv_kernel<8,double,double>",
                           "achieved": sb / t_spmv / 1e9, "peak": gbs_peak, "unit": "GB/s",
                           "frac": sb / t_spmv / 1e9 / gbs_peak, "algorithmic_bytes": sb, "launch_s": t_spmv},
+        "breakdown": breakdown,
         "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
         "gpu_launches": int(launches32),
         "generate_s": gen_s,

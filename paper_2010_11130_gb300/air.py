@@ -22,7 +22,7 @@ AIR_PREC_F32 = 1
 
 EXPORTED = ["air_default_options", "air_setup", "air_vcycle", "air_spmv", "air_gmres_solve",
             "air_hierarchy_levels", "air_hierarchy_info", "air_hierarchy_export", "air_free",
-            "air_status_string", "air_kernel_launches", "air_gmres_solve_noalloc"]
+            "air_status_string", "air_kernel_launches", "air_gmres_solve_noalloc", "air_setup_timings"]
 
 
 class air_csr(C.Structure):
@@ -81,6 +81,8 @@ def lib() -> C.CDLL:
     L.air_gmres_solve_noalloc.argtypes = [C.POINTER(air_csr), C.c_void_p, C.c_void_p, C.c_void_p,
                                           C.c_double, C.c_void_p, C.POINTER(air_solve_info)]
     L.air_gmres_solve_noalloc.restype = C.c_int
+    L.air_setup_timings.argtypes = [C.c_void_p, C.POINTER(C.c_double), C.c_int]
+    L.air_setup_timings.restype = C.c_int
     L.air_hierarchy_levels.argtypes = [C.c_void_p]
     L.air_hierarchy_levels.restype = C.c_int
     L.air_hierarchy_info.argtypes = [C.c_void_p, C.c_int, C.POINTER(air_level_info)]
@@ -173,6 +175,15 @@ class Hierarchy:
     @property
     def handle(self):
         return self._h
+
+    PHASES = ("strength", "transpose", "splitting", "lair", "onepoint_P", "rap", "coarsest", "other",
+              "split_picks", "split_search_iters", "split_slow_picks")
+
+    def setup_timings(self) -> dict:
+        """Device milliseconds per setup phase (summed over levels)."""
+        buf = (C.c_double * 11)()
+        _check(lib().air_setup_timings(self._h, buf, 11), "air_setup_timings")
+        return {k: float(buf[i]) for i, k in enumerate(self.PHASES)}
 
     def levels(self) -> int:
         return lib().air_hierarchy_levels(self._h)

@@ -14,6 +14,7 @@
 static std::atomic<unsigned long long> g_launches{0};
 
 unsigned long long air_launch_counter_add(unsigned long long k) { return g_launches.fetch_add(k) + k; }
+void air_launch_counter_sub(unsigned long long k) { g_launches.fetch_sub(k); }
 
 namespace {
 
@@ -56,7 +57,7 @@ void free_level(AirLevel &L) {
     L.rp = nullptr; L.ci = nullptr; L.v = nullptr;
     dfree(L.v32); dfree(L.dinv); dfree(L.dinv32);
     dfree(L.srp); dfree(L.sci);
-    dfree(L.cf); dfree(L.cid); dfree(L.crows);
+    dfree(L.cf); dfree(L.cid); dfree(L.crows); dfree(L.frows);
     dfree(L.rrp); dfree(L.rci); dfree(L.rv); dfree(L.rv32);
     dfree(L.pcol);
     dfree(L.b); dfree(L.x); dfree(L.x2);
@@ -71,17 +72,49 @@ void free_workspace(air_hierarchy *H) {
     H->ws_m = 0;
 }
 
-// First-pass kernel variant: 2 (default) exact bitmaps + two-hop lists +
-// int8 measures; 1 lazy bitmaps with L1-cached loads; 0 lazy bitmaps with
-// L2-only loads.  Set by the environment variable AIR_RS_VARIANT.
+// First-pass kernel variant: 2 (default, fastest measured) exact bitmaps,
+// two-hop lists and int8 measures with warp-combined read-modify-writes;
+// 3 one round trip of loads per pick with atomic bitmap updates; 1 lazy
+// bitmaps with L1-cached loads; 0 lazy bitmaps with L2-only loads.  All give
+// the same splitting.  Set by the environment variable AIR_RS_VARIANT.
 int rs_cached() {
     static int v = -1;
     if (v < 0) {
         const char *e = getenv("AIR_RS_VARIANT");
-        v = (e && (e[0] == '0' || e[0] == '1')) ? e[0] - '0' : 2;
+        v = (e && e[0] >= '0' && e[0] <= '3') ? e[0] - '0' : 2;
     }
     return v;
 }
+
+// CUDA-event phase timer accumulated into H->phase_ms (read after setup's syncs).
+struct PhaseTimer {
+    air_hierarchy *H;
+    cudaStream_t s;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    int cur = -1;
+    PhaseTimer(air_hierarchy *h, cudaStream_t st) : H(h), s(st) {
+        cudaEventCreate(&ev[0]);
+        cudaEventCreate(&ev[1]);
+    }
+    ~PhaseTimer() {
+        stop();
+        cudaEventDestroy(ev[0]);
+        cudaEventDestroy(ev[1]);
+    }
+    void start(int phase) {
+        stop();
+        cur = phase;
+        cudaEventRecord(ev[0], s);
+    }
+    void stop() {
+        if (cur < 0) return;
+        cudaEventRecord(ev[1], s);
+        cudaEventSynchronize(ev[1]);
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ev[0], ev[1]) == cudaSuccess) H->phase_ms[cur] += ms;
+        cur = -1;
+    }
+};
 
 // Build level l+1 from level l.  Returns AIR_OK with *stop = 1 when level l
 // is the coarsest.
@@ -90,6 +123,8 @@ int coarsen(air_hierarchy *H, int l, cudaStream_t s, int *stop) {
     const air_options &o = H->opt;
     int64_t n = L.n;
     *stop = 0;
+    PhaseTimer T(H, s);
+    T.start(0);
     // a1 strength
     int32_t *cnt = nullptr;
     AIR_TRY(dalloc(&cnt, n + 1));
@@ -106,6 +141,7 @@ int coarsen(air_hierarchy *H, int l, cudaStream_t s, int *stop) {
     AIR_TRY(dalloc(&L.sci, L.nnz_s));
     AIR_TRY(air_strength(L, o.theta, L.srp, L.sci, nullptr, 1, s));
     // a2 transpose
+    T.start(1);
     int64_t *strp = nullptr;
     int32_t *stci = nullptr;
     AIR_TRY(dalloc(&strp, n + 1));
@@ -118,8 +154,10 @@ int coarsen(air_hierarchy *H, int l, cudaStream_t s, int *stop) {
     AIR_CUDA(cudaMemcpyAsync(&max_st, dmax, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     AIR_CUDA(cudaStreamSynchronize(s));
     // a3 C/F splitting
+    T.start(2);
     AIR_TRY(dalloc(&L.cf, n));
-    AIR_TRY(air_rs_first_pass(n, L.srp, L.sci, strp, stci, max_st, max_s, L.cf, H->d_err, rs_cached(), s));
+    AIR_TRY(air_rs_first_pass(n, L.srp, L.sci, strp, stci, max_st, max_s, L.cf, H->d_err, rs_cached(), H->d_stats,
+                              s));
     AIR_TRY(check_err(H, s));
     dfree(strp);
     dfree(stci);
@@ -138,7 +176,11 @@ int coarsen(air_hierarchy *H, int l, cudaStream_t s, int *stop) {
     L.nc = nc;
     AIR_TRY(dalloc(&L.crows, nc));
     AIR_TRY(air_coarse_ids(n, L.cf, L.cid, L.crows, scanw, &nc, s));
+    L.nf = n - nc;
+    AIR_TRY(dalloc(&L.frows, L.nf));
+    AIR_TRY(air_point_list(n, L.cf, 0, L.frows, scanw, s));
     // a4 l-AIR restriction
+    T.start(3);
     AIR_TRY(air_lair_counts(nc, L.crows, L.srp, L.sci, L.cf, cnt, s));
     AIR_TRY(dalloc(&L.rrp, nc + 1));
     AIR_TRY(air_exclusive_scan_i32(cnt, L.rrp, nc, s));
@@ -157,9 +199,11 @@ int coarsen(air_hierarchy *H, int l, cudaStream_t s, int *stop) {
     AIR_TRY(read_i64(dsing, &L.n_singular, s));
     dfree(dsing);
     // a5 one-point interpolation
+    T.start(4);
     AIR_TRY(dalloc(&L.pcol, n));
     AIR_TRY(air_onepoint_P(L, o.theta, s));
     // a6 Galerkin product
+    T.start(5);
     AIR_TRY(air_rap_terms(L, cnt, s));
     AIR_CUDA(cudaMemsetAsync(dmax, 0, sizeof(int32_t), s));
     AIR_TRY(air_reduce_max_i32(cnt, nc, dmax, s));
@@ -192,6 +236,8 @@ int setup_impl(const air_csr *A, const air_options *opt, cudaStream_t s, air_hie
     AIR_CUDA(cudaGetDevice(&H->dev));
     AIR_TRY(dalloc(&H->d_err, 1));
     AIR_CUDA(cudaMemsetAsync(H->d_err, 0, sizeof(int), s));
+    AIR_TRY(dalloc(&H->d_stats, 4));
+    AIR_CUDA(cudaMemsetAsync(H->d_stats, 0, 4 * sizeof(unsigned long long), s));
     AirLevel &L0 = H->lev[0];
     L0.n = A->n_rows;
     L0.nnz = A->nnz;
@@ -230,6 +276,8 @@ int setup_impl(const air_csr *A, const air_options *opt, cudaStream_t s, air_hie
     AirLevel &Lc = H->lev[H->nlev - 1];
     H->nco = Lc.n;
     if (Lc.n > opt->max_dense) return AIR_ERR_COARSE_TOO_LARGE;
+    PhaseTimer T(H, s);
+    T.start(6);
     {
         double *work = nullptr;
         int64_t n = Lc.n;
@@ -239,10 +287,21 @@ int setup_impl(const air_csr *A, const air_options *opt, cudaStream_t s, air_hie
         cudaFreeAsync(work, s);
         AIR_TRY(check_err(H, s));
     }
+    {
+        unsigned long long st[4] = {0, 0, 0, 0};
+        AIR_CUDA(cudaMemcpyAsync(st, H->d_stats, sizeof(st), cudaMemcpyDeviceToHost, s));
+        AIR_CUDA(cudaStreamSynchronize(s));
+        H->phase_ms[8] = (double)st[0];
+        H->phase_ms[9] = (double)st[1];
+        H->phase_ms[10] = (double)st[2];
+    }
     // smoother diagonals, precision copies, V-cycle vectors
+    T.start(7);
     int f32 = opt->precision == AIR_PREC_F32;
     for (int q = 0; q < H->nlev; ++q) {
         AirLevel &L = H->lev[q];
+        AIR_TRY(air_max_row(L.n, L.rp, &L.maxrow, s));
+        if (q + 1 < H->nlev) AIR_TRY(air_max_row(L.nc, L.rrp, &L.maxrow_r, s));
         if (q + 1 < H->nlev) {
             AIR_TRY(dalloc(&L.dinv, L.n));
             if (f32) AIR_TRY(dalloc(&L.dinv32, L.n));
@@ -320,7 +379,7 @@ int gmres_impl(const AirLevel &A0, const air_hierarchy *Hc, const double *b, dou
     int it = 0;
     for (;;) {
         // r = b - A x into V_0 and its norm
-        AIR_TRY(air_spmv_f64(n, A0.rp, A0.ci, A0.v, x, H->V, b, s));
+        AIR_TRY(air_spmv_f64(n, A0.rp, A0.ci, A0.v, x, H->V, b, s, A0.nnz, A0.maxrow));
         AIR_TRY(norm2(n, H->V, H->partials, nblk, sc + 3, s));
         AIR_CUDA(cudaMemcpyAsync(H->h_est + 3, sc + 3, sizeof(double), cudaMemcpyDeviceToHost, s));
         AIR_CUDA(cudaStreamSynchronize(s));
@@ -336,7 +395,7 @@ int gmres_impl(const AirLevel &A0, const air_hierarchy *Hc, const double *b, dou
             double *vj = H->V + (int64_t)j * n, *zj = H->Z + (int64_t)j * n, *w = H->V + (int64_t)(j + 1) * n;
             AIR_TRY(air_vcycle_run(H, vj, zj, s));
             info->vcycles++;
-            AIR_TRY(air_spmv_f64(n, A0.rp, A0.ci, A0.v, zj, w, nullptr, s));
+            AIR_TRY(air_spmv_f64(n, A0.rp, A0.ci, A0.v, zj, w, nullptr, s, A0.nnz, A0.maxrow));
             // classical Gram-Schmidt, twice
             AIR_TRY(air_dot_partials(n, H->V, n, j + 1, w, H->partials, nblk, s));
             AIR_TRY(air_reduce_partials(j + 1, H->partials, nblk, h1, s));
@@ -420,7 +479,7 @@ int air_vcycle(const air_hierarchy *H, const double *b, double *x, void *stream)
 
 int air_spmv(const air_csr *A, const double *x, double *y, void *stream) {
     if (!A || !x || !y || !A->on_device || A->n_rows <= 0) return AIR_ERR_INVALID_ARG;
-    return air_spmv_f64(A->n_rows, A->row_ptr, A->col, A->val, x, y, nullptr, (cudaStream_t)stream);
+    return air_spmv_f64(A->n_rows, A->row_ptr, A->col, A->val, x, y, nullptr, (cudaStream_t)stream, A->nnz, 0);
 }
 
 int air_gmres_solve(const air_csr *A, const air_hierarchy *H, const double *b, double *x, double rtol, void *stream,
@@ -448,6 +507,12 @@ int air_gmres_solve(const air_csr *A, const air_hierarchy *H, const double *b, d
 }
 
 int air_hierarchy_levels(const air_hierarchy *H) { return H ? H->nlev : 0; }
+
+int air_setup_timings(const air_hierarchy *H, double *ms, int count) {
+    if (!H || !ms || count < 0) return AIR_ERR_INVALID_ARG;
+    for (int i = 0; i < count && i < 11; ++i) ms[i] = H->phase_ms[i];
+    return AIR_OK;
+}
 
 int air_hierarchy_info(const air_hierarchy *H, int level, air_level_info *info) {
     if (!H || !info || level < 0 || level >= H->nlev) return AIR_ERR_INVALID_ARG;
@@ -495,9 +560,12 @@ void air_free(air_hierarchy *H) {
     if (cur != H->dev) cudaSetDevice(H->dev);
     cudaDeviceSynchronize();
     for (int l = 0; l < AIR_MAX_LEVELS; ++l) free_level(H->lev[l]);
+    if (H->vgraph) cudaGraphExecDestroy(H->vgraph);
+    H->vgraph = nullptr;
     dfree(H->cinv);
     dfree(H->cinv32);
     dfree(H->d_err);
+    dfree(H->d_stats);
     dfree(H->xd);
     dfree(H->bd);
     free_workspace(H);

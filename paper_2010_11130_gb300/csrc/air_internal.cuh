@@ -30,6 +30,7 @@
 // Every kernel launch passes its grid size through air_counted(), which
 // counts the launch (host-side, for diagnostics) and returns the size.
 unsigned long long air_launch_counter_add(unsigned long long k);
+void air_launch_counter_sub(unsigned long long k);
 inline dim3 air_counted(dim3 g) {
     air_launch_counter_add(1);
     return g;
@@ -42,6 +43,7 @@ inline dim3 air_counted(dim3 g) {
 
 struct AirLevel {
     int64_t n = 0, nnz = 0;
+    int32_t maxrow = 0, maxrow_r = 0; // longest row of A_l and of R_l
     const int64_t *rp = nullptr;      // A_l (level 0 may alias the caller)
     const int32_t *ci = nullptr;
     const double *v = nullptr;
@@ -58,6 +60,8 @@ struct AirLevel {
     int32_t *cid = nullptr;           // coarse id or -1
     int64_t nc = 0;
     int32_t *crows = nullptr;         // C points ascending (nc)
+    int32_t *frows = nullptr;         // F points ascending (nf)
+    int64_t nf = 0;
     // restriction
     int64_t nnz_r = 0;
     int64_t *rrp = nullptr;
@@ -83,6 +87,13 @@ struct air_hierarchy {
     float *cinv32 = nullptr;
     // device scalars and scratch
     int *d_err = nullptr;
+    unsigned long long *d_stats = nullptr;   // first-pass counters: picks, search iterations, slow picks
+    // V-cycle body captured as a CUDA graph on first use
+    cudaGraphExec_t vgraph = nullptr;
+    int vgraph_failed = 0;
+    long long vgraph_kernels = 0;
+    // setup phase times (ms): strength, transpose, splitting, l-AIR, P, RAP, coarsest, other
+    double phase_ms[12] = {0};
     // GMRES workspace (allocated on first solve)
     int64_t ws_n = 0;
     int ws_m = 0;
@@ -111,7 +122,7 @@ int air_transpose_pattern(int64_t n, int64_t nnz, const int64_t *srp, const int3
                           int32_t *stci, int32_t *work, cudaStream_t s);
 int air_rs_first_pass(int64_t n, const int64_t *srp, const int32_t *sci, const int64_t *strp,
                       const int32_t *stci, int32_t max_st, int32_t max_s, int8_t *cf, int *d_err, int cached,
-                      cudaStream_t s);
+                      unsigned long long *stats, cudaStream_t s);
 int air_coarse_ids(int64_t n, const int8_t *cf, int32_t *cid, int32_t *crows, int64_t *work, int64_t *nc,
                    cudaStream_t s);
 int air_lair_counts(int64_t nc, const int32_t *crows, const int64_t *srp, const int32_t *sci, const int8_t *cf,
@@ -125,9 +136,12 @@ int air_coarse_inverse(int64_t n, const int64_t *rp, const int32_t *ci, const do
                        double *work, int *d_err, cudaStream_t s);
 
 // solve_kernels.cu
+// y = A x, or y = b - A x if b != NULL; nnz < 0 / maxrow <= 0 when unknown
 int air_spmv_f64(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, const double *x,
-                 double *y, const double *b, cudaStream_t s);   // y = A x, or y = b - A x if b != NULL
-int air_vcycle_run(const air_hierarchy *H, const double *b, double *x, cudaStream_t s);
+                 double *y, const double *b, cudaStream_t s, int64_t nnz = -1, int32_t maxrow = 0);
+int air_max_row(int64_t n, const int64_t *rp, int32_t *out_max, cudaStream_t s);
+int air_vcycle_run(const air_hierarchy *H, const double *b, double *x, cudaStream_t s, int use_graph = 1);
+int air_point_list(int64_t n, const int8_t *cf, int which, int32_t *list, int64_t *work, cudaStream_t s);
 int air_cast_d2f(const double *in, float *out, int64_t n, cudaStream_t s);
 int air_diag_inverse(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, double *dinv,
                      float *dinv32, cudaStream_t s);

@@ -125,7 +125,7 @@ extern "C" int air_gmres_solve_noalloc(const air_csr *A, const air_hierarchy *H,
     }
     int it = 0;
     for (;;) {
-        AIR_TRY(air_spmv_f64(n, A0.rp, A0.ci, A0.v, x, w.V, b, s));
+        AIR_TRY(air_spmv_f64(n, A0.rp, A0.ci, A0.v, x, w.V, b, s, A0.nnz, A0.maxrow));
         AIR_TRY(norm2(n, w.V, w.partials, nblk, w.sc + 3, s));
         AIR_TRY(read_scalars(w.sc + 3, hs + 3, 1, s));
         double beta = sqrt(hs[3]);
@@ -138,9 +138,9 @@ extern "C" int air_gmres_solve_noalloc(const air_csr *A, const air_hierarchy *H,
         int k = 0;
         for (int j = 0; j < m && it < H->opt.max_iter; ++j) {
             double *vj = w.V + (int64_t)j * n, *zj = w.Z + (int64_t)j * n, *wj = w.V + (int64_t)(j + 1) * n;
-            AIR_TRY(air_vcycle_run(H, vj, zj, s));
+            AIR_TRY(air_vcycle_run(H, vj, zj, s, 0));   // no graph: instantiating one may allocate
             info->vcycles++;
-            AIR_TRY(air_spmv_f64(n, A0.rp, A0.ci, A0.v, zj, wj, nullptr, s));
+            AIR_TRY(air_spmv_f64(n, A0.rp, A0.ci, A0.v, zj, wj, nullptr, s, A0.nnz, A0.maxrow));
             AIR_TRY(air_dot_partials(n, w.V, n, j + 1, wj, w.partials, nblk, s));
             AIR_TRY(air_reduce_partials(j + 1, w.partials, nblk, w.h1, s));
             AIR_TRY(air_update_dot_partials(n, w.V, n, j + 1, w.h1, wj, w.partials, nblk, j + 1, s));

@@ -132,7 +132,34 @@ __global__ void max_i32_kernel(const int32_t *in, int64_t n, int32_t *out) {
     if ((threadIdx.x & 31) == 0) atomicMax(out, m);
 }
 
+__global__ void max_row_kernel(const int64_t *rp, int64_t n, int32_t *out) {
+    int32_t m = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        m = max(m, (int32_t)(rp[i + 1] - rp[i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
 }  // namespace
+
+// Longest row of a CSR row pointer (synchronises the stream to read it).
+int air_max_row(int64_t n, const int64_t *rp, int32_t *out_max, cudaStream_t s) {
+    *out_max = 0;
+    if (n <= 0) return AIR_OK;
+    int32_t *d = nullptr;
+    AIR_CUDA(cudaMallocAsync(&d, sizeof(int32_t), s));
+    AIR_CUDA(cudaMemsetAsync(d, 0, sizeof(int32_t), s));
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    max_row_kernel<<<air_counted((unsigned)blocks), 256, 0, s>>>(rp, n, d);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out_max, d, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(d, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return AIR_ERR_CUDA;
+    return AIR_OK;
+}
 
 int air_exclusive_scan_i32(const int32_t *in, int64_t *out, int64_t n, cudaStream_t s) {
     return scan_impl<int32_t>(in, out, n, s);

@@ -40,65 +40,73 @@ __device__ __forceinline__ A seg_sum(A s) {
     return s;
 }
 
-// y = A x   or   y = b - A x      (VL lanes per row)
-template <int VL, typename TV, typename TX>
-__global__ void __launch_bounds__(256) spmv_kernel(int64_t n, const int64_t *__restrict__ rp,
-                                                   const int32_t *__restrict__ ci, const TV *__restrict__ v,
-                                                   const TX *__restrict__ x, TX *__restrict__ y,
-                                                   const TX *__restrict__ b) {
+// Row kernels (SpMV and masked Jacobi).  VL lanes share a row; each lane
+// owns U entries of it, so all column / value loads of the row and then all
+// x gathers are in flight together (the short HDG rows are otherwise
+// latency-bound).  Entries beyond U*VL fall to a remainder loop.  The loop
+// runs over blocks of rows with a trip count that is uniform across the
+// warp, so every lane reaches the segment shuffles.
+enum { ROW_SPMV = 0, ROW_JACOBI = 1 };
+
+template <typename TV, typename TX>
+struct RowArgs {
+    int64_t n;
+    const int64_t *rp;
+    const int32_t *ci;
+    const TV *v;
+    const TX *x;        // input vector (gathered)
+    TX *y;              // output
+    const TX *b;        // SpMV: optional (y = b - A x); Jacobi: right-hand side
+    const TX *dinv;     // Jacobi: 1 / a_ii
+    const int32_t *rows;  // Jacobi: the rows of the relaxed point set (ascending); n = their count
+    TX omega;
+};
+
+template <int VL, int U, typename TV, typename TX, int MODE>
+__global__ void __launch_bounds__(256) row_kernel(RowArgs<TV, TX> a) {
     using A = typename Acc<TX>::type;
-    int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / VL;
-    int lane = threadIdx.x & (VL - 1);
-    int64_t ng = ((int64_t)gridDim.x * blockDim.x) / VL;
-    for (int64_t row = g; row < n; row += ng) {
-        A s = 0;
-        for (int64_t e = rp[row] + lane; e < rp[row + 1]; e += VL) s += (A)v[e] * (A)x[ci[e]];
-        s = seg_sum<VL, A>(s);
-        if (lane == 0) y[row] = b ? (TX)((A)b[row] - s) : (TX)s;
+    const int lane = threadIdx.x & (VL - 1);
+    const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / VL;
+    const int64_t ng = ((int64_t)gridDim.x * blockDim.x) / VL;
+    const int64_t gw = g0 - (threadIdx.x & 31) / VL;            // first group of this warp
+    for (int64_t base = gw; base < a.n; base += ng) {
+        const int64_t pos = base + (g0 - gw);
+        const bool valid = pos < a.n;
+        int64_t row = pos;
+        if (MODE == ROW_JACOBI && valid) row = a.rows[pos];
+        A acc = 0;
+        if (valid) {
+            const int64_t rs = a.rp[row], re = a.rp[row + 1];
+            int32_t cols[U];
+            TV vals[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int64_t e = rs + lane + (int64_t)u * VL;
+                const bool ok = e < re;
+                cols[u] = ok ? __ldg(a.ci + e) : 0;
+                vals[u] = ok ? __ldg(a.v + e) : (TV)0;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) acc += (A)vals[u] * (A)__ldg(a.x + cols[u]);
+            for (int64_t e = rs + lane + (int64_t)U * VL; e < re; e += VL) acc += (A)a.v[e] * (A)a.x[a.ci[e]];
+        }
+        acc = seg_sum<VL, A>(acc);
+        if (lane == 0 && valid) {
+            if (MODE == ROW_SPMV) {
+                a.y[row] = a.b ? (TX)((A)a.b[row] - acc) : (TX)acc;
+            } else {
+                // the new value goes to the compact buffer y[pos]; scatter_kernel writes it back
+                a.y[pos] = (TX)(a.x[row] + a.omega * ((TX)((A)a.b[row] - acc)) * a.dinv[row]);
+            }
+        }
     }
 }
 
-// One masked Jacobi sweep: rows with cf == which get
-//     x_new_i = x_i + omega (b_i - (A x)_i) / a_ii,
-// the others x_new_i = x_i.  With INTERP the input iterate is x = P x_c,
-// evaluated on the fly from the coarse vector through pcol (one-point P).
-template <int VL, typename T, bool INTERP>
-__global__ void __launch_bounds__(256) jacobi_kernel(int64_t n, const int64_t *__restrict__ rp,
-                                                     const int32_t *__restrict__ ci, const T *__restrict__ v,
-                                                     const T *__restrict__ dinv, const int8_t *__restrict__ cf,
-                                                     int which, T omega, const T *__restrict__ b,
-                                                     const T *__restrict__ xin, const int32_t *__restrict__ pcol,
-                                                     T *__restrict__ xout) {
-    int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / VL;
-    int lane = threadIdx.x & (VL - 1);
-    int64_t ng = ((int64_t)gridDim.x * blockDim.x) / VL;
-    for (int64_t row = g; row < n; row += ng) {
-        T xi;
-        if (INTERP) {
-            int32_t pc = pcol[row];
-            xi = pc >= 0 ? xin[pc] : (T)0;
-        } else {
-            xi = xin[row];
-        }
-        if (cf[row] != which) {
-            if (lane == 0) xout[row] = xi;
-            continue;
-        }
-        T s = 0;
-        for (int64_t e = rp[row] + lane; e < rp[row + 1]; e += VL) {
-            int32_t j = ci[e];
-            T xj;
-            if (INTERP) {
-                int32_t pc = pcol[j];
-                xj = pc >= 0 ? xin[pc] : (T)0;
-            } else {
-                xj = xin[j];
-            }
-            s += v[e] * xj;
-        }
-        s = seg_sum<VL, T>(s);
-        if (lane == 0) xout[row] = xi + omega * (b[row] - s) * dinv[row];
-    }
+// x[rows[pos]] = t[pos]: finishes one Jacobi sweep in place.
+template <typename T>
+__global__ void scatter_kernel(int64_t m, const int32_t *__restrict__ rows, const T *__restrict__ t, T *__restrict__ x) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < m; p += (int64_t)gridDim.x * blockDim.x)
+        x[rows[p]] = t[p];
 }
 
 template <typename T>
@@ -296,39 +304,50 @@ __global__ void axpy_multi_kernel(int64_t n, const double *__restrict__ Z, int64
 
 __global__ void set_scalar_kernel(double *p, double v) { *p = v; }
 
-template <int VL, typename TV, typename TX>
-void launch_spmv(int64_t n, const int64_t *rp, const int32_t *ci, const TV *v, const TX *x, TX *y, const TX *b,
-                 cudaStream_t s) {
-    unsigned g = grid_cap(n * VL, 256, 152 * 64);
-    spmv_kernel<VL, TV, TX><<<air_counted(g), 256, 0, s>>>(n, rp, ci, v, x, y, b);
+template <int U, typename TV, typename TX, int MODE>
+void launch_row(const RowArgs<TV, TX> &a, cudaStream_t s) {
+    unsigned g = grid_cap(a.n * 4, 256, 152 * 16);
+    row_kernel<4, U, TV, TX, MODE><<<air_counted(g), 256, 0, s>>>(a);
+}
+
+// Entries per lane: enough for the longest row when rows are at most 64
+// long, else for the average row with the remainder loop taking the rest.
+template <typename TV, typename TX, int MODE>
+void row_dispatch(const RowArgs<TV, TX> &a, int64_t nnz, int32_t maxrow, cudaStream_t s) {
+    double avg = a.n > 0 ? (double)nnz / (double)a.n : 0.0;
+    int want = maxrow > 0 && maxrow <= 64 ? (maxrow + 3) / 4 : (int)((avg * 1.25 + 3.0) / 4.0);
+    if (want <= 1) launch_row<1, TV, TX, MODE>(a, s);
+    else if (want <= 2) launch_row<2, TV, TX, MODE>(a, s);
+    else if (want <= 4) launch_row<4, TV, TX, MODE>(a, s);
+    else if (want <= 6) launch_row<6, TV, TX, MODE>(a, s);
+    else if (want <= 8) launch_row<8, TV, TX, MODE>(a, s);
+    else if (want <= 10) launch_row<10, TV, TX, MODE>(a, s);
+    else if (want <= 12) launch_row<12, TV, TX, MODE>(a, s);
+    else launch_row<16, TV, TX, MODE>(a, s);
 }
 
 template <typename TV, typename TX>
-void spmv_dispatch(int64_t n, int64_t nnz, const int64_t *rp, const int32_t *ci, const TV *v, const TX *x, TX *y,
-                   const TX *b, cudaStream_t s) {
-    double avg = n > 0 ? (double)nnz / (double)n : 0.0;
-    if (avg <= 4) launch_spmv<2>(n, rp, ci, v, x, y, b, s);
-    else if (avg <= 10) launch_spmv<4>(n, rp, ci, v, x, y, b, s);
-    else if (avg <= 40) launch_spmv<8>(n, rp, ci, v, x, y, b, s);
-    else launch_spmv<16>(n, rp, ci, v, x, y, b, s);
+void spmv_dispatch(int64_t n, int64_t nnz, int32_t maxrow, const int64_t *rp, const int32_t *ci, const TV *v,
+                   const TX *x, TX *y, const TX *b, cudaStream_t s) {
+    RowArgs<TV, TX> a{};
+    a.n = n; a.rp = rp; a.ci = ci; a.v = v; a.x = x; a.y = y; a.b = b;
+    row_dispatch<TV, TX, ROW_SPMV>(a, nnz, maxrow, s);
 }
 
-template <int VL, typename T, bool INTERP>
-void launch_jacobi(const AirLevel &L, const T *v, const T *dinv, int which, T omega, const T *b, const T *xin,
-                   T *xout, cudaStream_t s) {
-    unsigned g = grid_cap(L.n * VL, 256, 152 * 64);
-    jacobi_kernel<VL, T, INTERP><<<air_counted(g), 256, 0, s>>>(L.n, L.rp, L.ci, v, dinv, L.cf, which, omega, b, xin, L.pcol,
-                                                   xout);
-}
-
-template <typename T, bool INTERP>
-void jacobi_dispatch(const AirLevel &L, const T *v, const T *dinv, int which, T omega, const T *b, const T *xin,
-                     T *xout, cudaStream_t s) {
-    double avg = L.n > 0 ? (double)L.nnz / (double)L.n : 0.0;
-    if (avg <= 4) launch_jacobi<2, T, INTERP>(L, v, dinv, which, omega, b, xin, xout, s);
-    else if (avg <= 10) launch_jacobi<4, T, INTERP>(L, v, dinv, which, omega, b, xin, xout, s);
-    else if (avg <= 40) launch_jacobi<8, T, INTERP>(L, v, dinv, which, omega, b, xin, xout, s);
-    else launch_jacobi<16, T, INTERP>(L, v, dinv, which, omega, b, xin, xout, s);
+// One Jacobi sweep over the point set `which` (0 = F, 1 = C), in place on x:
+// new values of the set's rows go to tmp, then are scattered back.
+template <typename T>
+void jacobi_dispatch(const AirLevel &L, const T *v, const T *dinv, int which, T omega, const T *b, T *x, T *tmp,
+                     cudaStream_t s) {
+    const int32_t *rows = which ? L.crows : L.frows;
+    int64_t m = which ? L.nc : L.nf;
+    if (m == 0) return;
+    RowArgs<T, T> a{};
+    a.n = m; a.rp = L.rp; a.ci = L.ci; a.v = v; a.x = x; a.y = tmp; a.b = b; a.dinv = dinv; a.rows = rows;
+    a.omega = omega;
+    int64_t nnz_set = L.n > 0 ? (int64_t)((double)L.nnz * (double)m / (double)L.n) : 0;
+    row_dispatch<T, T, ROW_JACOBI>(a, nnz_set, L.maxrow, s);
+    scatter_kernel<T><<<air_counted(grid_cap(m, 256)), 256, 0, s>>>(m, rows, tmp, x);
 }
 
 template <typename T>
@@ -361,7 +380,8 @@ int vcycle_t(const air_hierarchy *H, const T *b0, T *x0, cudaStream_t s) {
     for (int l = 0; l + 1 < L; ++l) {
         const AirLevel &A = H->lev[l];
         const T *bl = l == 0 ? b0 : (const T *)A.b;
-        spmv_dispatch<T, T>(A.nc, A.nnz_r, A.rrp, A.rci, lvl_rvals<T>(A), bl, (T *)H->lev[l + 1].b, nullptr, s);
+        spmv_dispatch<T, T>(A.nc, A.nnz_r, A.maxrow_r, A.rrp, A.rci, lvl_rvals<T>(A), bl, (T *)H->lev[l + 1].b,
+                            nullptr, s);
     }
     // coarsest: x = A_L^{-1} b
     {
@@ -379,21 +399,13 @@ int vcycle_t(const air_hierarchy *H, const T *b0, T *x0, cudaStream_t s) {
         T *out = l == 0 ? x0 : (T *)A.x;
         T *alt = (T *)A.x2;
         const T *xc = (const T *)H->lev[l + 1].x;
-        if (ns == 0) {
-            interp_kernel<T><<<air_counted(grid_cap(A.n, 256)), 256, 0, s>>>(A.n, A.pcol, xc, out);
-            continue;
-        }
+        // x = P x_c, then the sweeps in place
+        interp_kernel<T><<<air_counted(grid_cap(A.n, 256)), 256, 0, s>>>(A.n, A.pcol, xc, out);
         const T *v = lvl_vals<T>(A);
         const T *dinv = lvl_dinv<T>(A);
-        const T *cur = xc;
         for (int q = 0; q < ns; ++q) {
-            T *dst = ((ns - 1 - q) % 2 == 0) ? out : alt;
             int which = relax[q] == 'C' ? 1 : 0;
-            if (q == 0)
-                jacobi_dispatch<T, true>(A, v, dinv, which, omega, bl, cur, dst, s);
-            else
-                jacobi_dispatch<T, false>(A, v, dinv, which, omega, bl, cur, dst, s);
-            cur = dst;
+            jacobi_dispatch<T>(A, v, dinv, which, omega, bl, out, alt, s);
         }
     }
     AIR_LAUNCH();
@@ -403,19 +415,69 @@ int vcycle_t(const air_hierarchy *H, const T *b0, T *x0, cudaStream_t s) {
 }  // namespace
 
 int air_spmv_f64(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, const double *x, double *y,
-                 const double *b, cudaStream_t s) {
-    // 8 lanes per row: the trace systems hold 9 to 61 entries per row.
-    launch_spmv<8, double, double>(n, rp, ci, v, x, y, b, s);
+                 const double *b, cudaStream_t s, int64_t nnz, int32_t maxrow) {
+    if (nnz < 0) nnz = 40 * n;      // unknown: sized for the 2D+time p = 2 rows, remainder loop for longer ones
+    spmv_dispatch<double, double>(n, nnz, maxrow, rp, ci, v, x, y, b, s);
     AIR_LAUNCH();
     return AIR_OK;
 }
 
-int air_vcycle_run(const air_hierarchy *H, const double *b, double *x, cudaStream_t s) {
-    if (H->opt.precision == AIR_PREC_F64) return vcycle_t<double>(H, b, x, s);
+// The V-cycle body (from the finest-level buffers lev[0].b to lev[0].x) is
+// captured once into a CUDA graph on a private stream and replayed on the
+// caller's stream; only the conversion in and out of lev[0] runs outside it.
+template <typename T>
+int vcycle_graph(air_hierarchy *H, cudaStream_t s) {
     const AirLevel &L0 = H->lev[0];
+    if (!H->vgraph && !H->vgraph_failed) {
+        cudaStream_t cs = nullptr;
+        AIR_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaGraph_t g = nullptr;
+        unsigned long long c0 = air_launch_counter_add(0);
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            int st = vcycle_t<T>(H, (const T *)L0.b, (T *)L0.x, cs);
+            e = cudaStreamEndCapture(cs, &g);
+            if (st != AIR_OK && e == cudaSuccess) e = cudaErrorUnknown;
+        }
+        unsigned long long c1 = air_launch_counter_add(0);
+        air_launch_counter_sub(c1 - c0);   // captured, not yet run
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&H->vgraph, g, 0);
+        if (g) cudaGraphDestroy(g);
+        cudaStreamDestroy(cs);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            H->vgraph = nullptr;
+            H->vgraph_failed = 1;
+        } else {
+            H->vgraph_kernels = (long long)(c1 - c0);
+        }
+    }
+    if (H->vgraph) {
+        AIR_CUDA(cudaGraphLaunch(H->vgraph, s));
+        air_launch_counter_add((unsigned long long)H->vgraph_kernels);
+        return AIR_OK;
+    }
+    return vcycle_t<T>(H, (const T *)L0.b, (T *)L0.x, s);
+}
+
+int air_vcycle_run(const air_hierarchy *Hc, const double *b, double *x, cudaStream_t s, int use_graph) {
+    air_hierarchy *H = const_cast<air_hierarchy *>(Hc);
+    const AirLevel &L0 = H->lev[0];
+    if (H->opt.precision == AIR_PREC_F64) {
+        if (!use_graph) return vcycle_t<double>(H, b, x, s);
+        AIR_CUDA(cudaMemcpyAsync(L0.b, b, (size_t)L0.n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        AIR_TRY(vcycle_graph<double>(H, s));
+        AIR_CUDA(cudaMemcpyAsync(x, L0.x, (size_t)L0.n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        return AIR_OK;
+    }
     float *b32 = (float *)L0.b, *x32 = (float *)L0.x;
     d2f_kernel<<<air_counted(grid_cap(L0.n, 256)), 256, 0, s>>>(b, b32, L0.n);
-    AIR_TRY(vcycle_t<float>(H, b32, x32, s));
+    AIR_LAUNCH();
+    if (use_graph) {
+        AIR_TRY(vcycle_graph<float>(H, s));
+    } else {
+        AIR_TRY(vcycle_t<float>(H, b32, x32, s));
+    }
     f2d_kernel<<<air_counted(grid_cap(L0.n, 256)), 256, 0, s>>>(x32, x, L0.n);
     AIR_LAUNCH();
     return AIR_OK;
