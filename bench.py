@@ -129,7 +129,7 @@ class ClockSampler:
 
 
 # ------------------------------------------------------- algorithmic bytes
-def vcycle_bytes(H, wbytes):
+def vcycle_bytes(H, wbytes, diag_bytes=0):
     """Algorithmic DRAM bytes of one V-cycle: each array read once per use.
 
     Per non-coarsest level (n rows, nnz z = z_F + z_C, R with nnz_R entries,
@@ -138,7 +138,9 @@ def vcycle_bytes(H, wbytes):
       F sweep (+P)  z_F (w+4) + 8 n_F + 4 n + w n_C + 2 w n_F + n + w n
       C sweep       z_C (w+4) + 8 n_C + w n + 2 w n_C + n + w n
       F sweep       z_F (w+4) + 8 n_F + w n + 2 w n_F + n + w n
-    coarsest: w n_L^2 + 2 w n_L.
+    coarsest: w n_L^2 + 2 w n_L.  BF16 storage (w = 2) adds the FP32
+    diagonal (4 B per relaxed row) and keeps FP32 vectors (counted as w = 4
+    for vectors).
     """
     total = 0
     L = H.levels()
@@ -146,7 +148,8 @@ def vcycle_bytes(H, wbytes):
         inf = H.info(l)
         n = inf.n
         if inf.coarsest:
-            total += wbytes * n * n + 2 * wbytes * n
+            xb = 4 if wbytes == 2 else wbytes
+            total += xb * n * n + 2 * xb * n
             continue
         rp = H.export(l, "A.row_ptr")
         cf = H.export(l, "cf").astype(bool)
@@ -155,11 +158,12 @@ def vcycle_bytes(H, wbytes):
         zf = int(rl[~cf].sum())
         nc = int(cf.sum())
         nf = n - nc
-        w = wbytes
-        total += inf.nnz_r * (w + 4) + 8 * nc + w * n + w * nc
-        total += zf * (w + 4) + 8 * nf + 4 * n + w * nc + 2 * w * nf + n + w * n
-        total += zc * (w + 4) + 8 * nc + w * n + 2 * w * nc + n + w * n
-        total += zf * (w + 4) + 8 * nf + w * n + 2 * w * nf + n + w * n
+        w = wbytes                       # stored value bytes
+        x = 4 if wbytes == 2 else wbytes  # vector element bytes
+        total += inf.nnz_r * (w + 4) + 8 * nc + x * n + x * nc
+        total += zf * (w + 4) + 8 * nf + 4 * n + x * nc + 2 * x * nf + n + x * n + diag_bytes * nf
+        total += zc * (w + 4) + 8 * nc + x * n + 2 * x * nc + n + x * n + diag_bytes * nc
+        total += zf * (w + 4) + 8 * nf + x * n + 2 * x * nf + n + x * n + diag_bytes * nf
     return total
 
 
@@ -257,14 +261,14 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def timed(prec):
-        for _ in range(args.warmup):
+    def timed(prec, warmup, steps):
+        for _ in range(warmup):
             step(prec)
         barrier()
         k0 = air.kernel_launches()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        infos = [step(prec) for _ in range(args.steps)]
+        infos = [step(prec) for _ in range(steps)]
         e1.record(stream)
         barrier()
         ms = e0.elapsed_time(e1)
@@ -272,19 +276,22 @@ def run_ours(args):
             t = torch.tensor([ms], device="cuda")
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             ms = float(t.item())
-        return ms / args.steps, infos, air.kernel_launches() - k0
+        return ms / steps, infos, air.kernel_launches() - k0
 
+    # the reported value: FP32 hierarchy inside FP64 FGMRES, W warm-up + K timed
+    # steps; the FP64 and BF16-off-diagonal forms get one warm-up and one step
     clocks = ClockSampler(local)
     clocks.start()
-    ms32, inf32, launches32 = timed(1)
-    ms64, inf64, launches64 = timed(0)
+    ms32, inf32, launches32 = timed(1, args.warmup, args.steps)
     clk = clocks.stop()
+    ms64, inf64, _ = timed(0, 1, 1)
+    ms16, inf16, _ = timed(2, 1, 1)
 
     # V-cycle and SpMV roofline (FP32 hierarchy is the reported form)
     gbs_peak, peak_kind = peaks()
     rl = {}
     breakdown = {}
-    for prec, key in ((1, "f32"), (0, "f64")):
+    for prec, key in ((1, "f32"), (0, "f64"), (2, "bf16")):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         H = air.setup(A, theta=0.25, distance=1, precision=prec)
@@ -297,7 +304,7 @@ def run_ours(args):
         t_solve = time.perf_counter() - t0
         breakdown[key] = {"setup_s": t_setup, "solve_s": t_solve, "iters": inf_s.iters,
                           "setup_phase_ms": H.setup_timings(), "levels": H.levels()}
-        vb = vcycle_bytes(H, 4 if prec == 1 else 8)
+        vb = vcycle_bytes(H, {1: 4, 0: 8, 2: 2}[prec], diag_bytes=4 if prec == 2 else 0)
         xv = torch.empty_like(b)
         for _ in range(3):
             H.vcycle(b, xv)
@@ -335,7 +342,7 @@ def run_ours(args):
         Ah = air.CSR(rp_h, ci_h, v_h, s.n)
         torch.cuda.synchronize()
         tt = []
-        for _ in range(max(1, args.steps)):
+        for _ in range(1):
             t0 = time.perf_counter()
             Hh = air.setup(Ah, theta=0.25, distance=1, precision=1)
             _, ih = air.gmres_solve(Ah, Hh, b_h, x_h, rtol=args.rtol)
@@ -357,7 +364,9 @@ def run_ours(args):
             "f32_precond_fgmres": {"s": ms32 / 1e3, "iters": inf32[-1].iters, "relres": inf32[-1].relres,
                                    "vcycle_gbs": v32["gbs"]},
             "f64": {"s": ms64 / 1e3, "iters": inf64[-1].iters, "relres": inf64[-1].relres,
-                    "vcycle_gbs": rl["f64"]["gbs"]}},
+                    "vcycle_gbs": rl["f64"]["gbs"]},
+            "bf16_offdiag_precond_fgmres": {"s": ms16 / 1e3, "iters": inf16[-1].iters, "relres": inf16[-1].relres,
+                                            "vcycle_gbs": rl["bf16"]["gbs"]}},
         "roofline": {"bound": "hbm", "kernel": "V-cycle (FP32 hierarchy, all levels)",
                      "achieved": v32["gbs"], "peak": gbs_peak, "unit": "GB/s",
                      "frac": v32["gbs"] / gbs_peak, "traffic": None,

@@ -47,6 +47,7 @@ extern "C" {
 /* precision in which the hierarchy is stored and the V-cycle is applied */
 #define AIR_PREC_F64  0
 #define AIR_PREC_F32  1
+#define AIR_PREC_BF16 2   /* off-diagonal values of A_l and R_l in BF16, diagonals and vectors FP32 */
 
 typedef struct {
     int64_t n_rows, n_cols, nnz;
@@ -64,7 +65,7 @@ typedef struct {
     int max_coarse;      /* stop coarsening at or below this many rows */
     int max_levels;      /* hard cap on levels (<= 32) */
     int max_dense;       /* largest coarsest level inverted densely */
-    int precision;       /* AIR_PREC_F64 or AIR_PREC_F32 */
+    int precision;       /* AIR_PREC_F64, AIR_PREC_F32 or AIR_PREC_BF16 */
     int restart;         /* GMRES restart length m (<= 32) */
     int max_iter;        /* total inner GMRES steps */
     int validate;        /* 1: check the CSR before setup (one extra pass) */
@@ -112,8 +113,9 @@ int air_setup(const air_csr *A, double theta, int distance, const air_options *o
 
 /* One V-cycle x = M^{-1} b (Section 3, x <- x + P (RAP)^{-1} R r, applied
  * recursively from a zero guess, followed by the relax sweeps).  b and x are
- * device float64 vectors of length n; an F32 hierarchy converts at the
- * finest level.  Asynchronous on stream. */
+ * device float64 vectors of length n; an F32 or BF16 hierarchy converts
+ * at the finest level.  The first call captures the V-cycle into a CUDA
+ * graph (replayed by later calls).  Asynchronous on stream. */
 int air_vcycle(const air_hierarchy *H, const double *b, double *x, void *stream);
 
 /* y = A x for device CSR A and device vectors.  Asynchronous. */

@@ -19,6 +19,7 @@ AIR_OK = 0
 AIR_NOT_CONVERGED = 1
 AIR_PREC_F64 = 0
 AIR_PREC_F32 = 1
+AIR_PREC_BF16 = 2
 
 EXPORTED = ["air_default_options", "air_setup", "air_vcycle", "air_spmv", "air_gmres_solve",
             "air_hierarchy_levels", "air_hierarchy_info", "air_hierarchy_export", "air_free",

@@ -55,7 +55,7 @@ void free_level(AirLevel &L) {
         dfree(L.v);
     }
     L.rp = nullptr; L.ci = nullptr; L.v = nullptr;
-    dfree(L.v32); dfree(L.dinv); dfree(L.dinv32);
+    dfree(L.v32); dfree(L.dinv); dfree(L.dinv32); dfree(L.v16); dfree(L.diag32); dfree(L.rv16);
     dfree(L.srp); dfree(L.sci);
     dfree(L.cf); dfree(L.cid); dfree(L.crows); dfree(L.frows);
     dfree(L.rrp); dfree(L.rci); dfree(L.rv); dfree(L.rv32);
@@ -297,7 +297,8 @@ int setup_impl(const air_csr *A, const air_options *opt, cudaStream_t s, air_hie
     }
     // smoother diagonals, precision copies, V-cycle vectors
     T.start(7);
-    int f32 = opt->precision == AIR_PREC_F32;
+    int f32 = opt->precision != AIR_PREC_F64;      // FP32 vectors (F32 and BF16 storage)
+    int bf16 = opt->precision == AIR_PREC_BF16;
     for (int q = 0; q < H->nlev; ++q) {
         AirLevel &L = H->lev[q];
         AIR_TRY(air_max_row(L.n, L.rp, &L.maxrow, s));
@@ -306,7 +307,16 @@ int setup_impl(const air_csr *A, const air_options *opt, cudaStream_t s, air_hie
             AIR_TRY(dalloc(&L.dinv, L.n));
             if (f32) AIR_TRY(dalloc(&L.dinv32, L.n));
             AIR_TRY(air_diag_inverse(L.n, L.rp, L.ci, L.v, L.dinv, L.dinv32, s));
-            if (f32) {
+            if (bf16) {
+                uint16_t *v16 = nullptr, *r16 = nullptr;
+                AIR_TRY(dalloc(&v16, L.nnz));
+                AIR_TRY(dalloc(&L.diag32, L.n));
+                AIR_TRY(air_cast_bf16(L.n, L.rp, L.ci, L.v, v16, L.diag32, s));
+                AIR_TRY(dalloc(&r16, L.nnz_r));
+                AIR_TRY(air_cast_bf16(L.nc, L.rrp, L.rci, L.rv, r16, nullptr, s));
+                L.v16 = v16;
+                L.rv16 = r16;
+            } else if (f32) {
                 AIR_TRY(dalloc(&L.v32, L.nnz));
                 AIR_TRY(air_cast_d2f(L.v, L.v32, L.nnz, s));
                 AIR_TRY(dalloc(&L.rv32, L.nnz_r));
@@ -457,7 +467,7 @@ int air_setup(const air_csr *A, double theta, int distance, const air_options *o
         if (*c != 'F' && *c != 'C') return AIR_ERR_INVALID_ARG;
     if (!(theta >= 0.0) || !(theta <= 1.0) || o.max_levels < 1 || o.max_levels > AIR_MAX_LEVELS ||
         o.max_dense < 1 || o.restart < 1 || o.restart > 32 || o.max_iter < 0 ||
-        (o.precision != AIR_PREC_F64 && o.precision != AIR_PREC_F32))
+        (o.precision != AIR_PREC_F64 && o.precision != AIR_PREC_F32 && o.precision != AIR_PREC_BF16))
         return AIR_ERR_INVALID_ARG;
     if (distance != 1) return AIR_ERR_UNSUPPORTED;
     air_hierarchy *H = new (std::nothrow) air_hierarchy();

@@ -49,6 +49,8 @@ struct AirLevel {
     const double *v = nullptr;
     int owns_A = 0;
     float *v32 = nullptr;             // F32 copy of A_l values
+    void *v16 = nullptr;              // BF16 copy of A_l off-diagonal values (diagonal zeroed)
+    float *diag32 = nullptr;          // a_ii in FP32 (BF16 storage)
     double *dinv = nullptr;           // 1 / a_ii
     float *dinv32 = nullptr;
     // strength graph
@@ -68,6 +70,7 @@ struct AirLevel {
     int32_t *rci = nullptr;
     double *rv = nullptr;
     float *rv32 = nullptr;
+    void *rv16 = nullptr;
     int64_t n_singular = 0;
     int32_t max_m = 0;
     // one-point interpolation
@@ -143,6 +146,8 @@ int air_max_row(int64_t n, const int64_t *rp, int32_t *out_max, cudaStream_t s);
 int air_vcycle_run(const air_hierarchy *H, const double *b, double *x, cudaStream_t s, int use_graph = 1);
 int air_point_list(int64_t n, const int8_t *cf, int which, int32_t *list, int64_t *work, cudaStream_t s);
 int air_cast_d2f(const double *in, float *out, int64_t n, cudaStream_t s);
+int air_cast_bf16(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, void *out16, float *diag32,
+                  cudaStream_t s);
 int air_diag_inverse(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, double *dinv,
                      float *dinv32, cudaStream_t s);
 

@@ -4,10 +4,13 @@
 // round-to-nearest intrinsics (__dmul_rn, __dadd_rn, __dsub_rn, __ddiv_rn) so
 // that no multiply-add is contracted: strength tests, local LU solves and the
 // Galerkin sums reproduce a plain sequential FP64 evaluation bit for bit.
+#include <cooperative_groups.h>
 #include <float.h>
 #include <math.h>
 
 #include "air_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -1196,54 +1199,67 @@ __global__ void dense_absmax_kernel(int64_t n, const double *M, double *out) {
     }
 }
 
-__global__ void gj_pivot_kernel(int64_t n, int64_t k, double *M, double *fcol, const double *amax, int *err) {
-    __shared__ double sb[32];
-    __shared__ int64_t sr[32];
+// All pivot steps in one cooperative launch: block 0 picks the pivot row
+// (largest |entry| of the column, ties -> smallest row), swaps it up, scales
+// it and saves the column factors; then every block eliminates the column
+// from the other rows.  Grid-wide barriers separate the phases; a singular
+// pivot sets the error flag, which every block reads after the barrier, so
+// all blocks leave together.
+__global__ void __launch_bounds__(512) gj_coop_kernel(int64_t n, double *M, double *fcol, const double *amax,
+                                                      int *err) {
+    cg::grid_group grid = cg::this_grid();
+    __shared__ double sb[16];
+    __shared__ int64_t sr[16];
     __shared__ int64_t piv;
-    int tid = threadIdx.x;
-    double best = -1.0;
-    int64_t br = n;
-    for (int64_t r = k + tid; r < n; r += blockDim.x) {
-        double a = fabs(M[r * 2 * n + k]);
-        if (a > best) { best = a; br = r; }
-    }
+    const int tid = threadIdx.x;
+    const double tol = 1e-14 * amax[0];
+    for (int64_t k = 0; k < n; ++k) {
+        if (blockIdx.x == 0) {
+            double best = -1.0;
+            int64_t br = n;
+            for (int64_t r = k + tid; r < n; r += blockDim.x) {
+                double av = fabs(M[r * 2 * n + k]);
+                if (av > best) { best = av; br = r; }
+            }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        double ob = __shfl_xor_sync(FULL, best, o);
-        int64_t orr = __shfl_xor_sync(FULL, br, o);
-        if (ob > best || (ob == best && orr < br)) { best = ob; br = orr; }
-    }
-    if ((tid & 31) == 0) { sb[tid >> 5] = best; sr[tid >> 5] = br; }
-    __syncthreads();
-    if (tid == 0) {
-        for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
-            if (sb[w] > sb[0] || (sb[w] == sb[0] && sr[w] < sr[0])) { sb[0] = sb[w]; sr[0] = sr[w]; }
-        piv = sr[0];
-        if (!(sb[0] > 1e-14 * amax[0])) { atomicOr(err, AIR_DEVERR_SINGULAR); piv = -1; }
-    }
-    __syncthreads();
-    int64_t p = piv;
-    if (p < 0) return;
-    if (p != k)
-        for (int64_t c = k + tid; c < 2 * n; c += blockDim.x) {
-            double t1 = M[k * 2 * n + c];
-            M[k * 2 * n + c] = M[p * 2 * n + c];
-            M[p * 2 * n + c] = t1;
+            for (int o = 16; o > 0; o >>= 1) {
+                double ob = __shfl_xor_sync(FULL, best, o);
+                int64_t orr = __shfl_xor_sync(FULL, br, o);
+                if (ob > best || (ob == best && orr < br)) { best = ob; br = orr; }
+            }
+            if ((tid & 31) == 0) { sb[tid >> 5] = best; sr[tid >> 5] = br; }
+            __syncthreads();
+            if (tid == 0) {
+                for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+                    if (sb[w] > sb[0] || (sb[w] == sb[0] && sr[w] < sr[0])) { sb[0] = sb[w]; sr[0] = sr[w]; }
+                piv = sr[0];
+                if (!(sb[0] > tol)) { atomicOr(err, AIR_DEVERR_SINGULAR); piv = -1; }
+            }
+            __syncthreads();
+            const int64_t p = piv;
+            if (p >= 0) {
+                if (p != k)
+                    for (int64_t c = k + tid; c < 2 * n; c += blockDim.x) {
+                        double t1 = M[k * 2 * n + c];
+                        M[k * 2 * n + c] = M[p * 2 * n + c];
+                        M[p * 2 * n + c] = t1;
+                    }
+                __syncthreads();
+                const double d = M[k * 2 * n + k];
+                __syncthreads();
+                for (int64_t c = k + tid; c < 2 * n; c += blockDim.x) M[k * 2 * n + c] = M[k * 2 * n + c] / d;
+                for (int64_t r = tid; r < n; r += blockDim.x) fcol[r] = (r == k) ? 0.0 : M[r * 2 * n + k];
+            }
         }
-    __syncthreads();
-    double d = M[k * 2 * n + k];
-    __syncthreads();
-    for (int64_t c = k + tid; c < 2 * n; c += blockDim.x) M[k * 2 * n + c] = M[k * 2 * n + c] / d;
-    for (int64_t r = tid; r < n; r += blockDim.x) fcol[r] = (r == k) ? 0.0 : M[r * 2 * n + k];
-}
-
-__global__ void gj_eliminate_kernel(int64_t n, int64_t k, double *M, const double *fcol, const int *err) {
-    if (*err & AIR_DEVERR_SINGULAR) return;
-    int64_t w = 2 * n - k;
-    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n * w; s += (int64_t)gridDim.x * blockDim.x) {
-        int64_t r = s / w, c = k + s % w;
-        double f = fcol[r];
-        if (r != k && f != 0.0) M[r * 2 * n + c] -= f * M[k * 2 * n + c];
+        grid.sync();
+        if (__ldcg(err) & AIR_DEVERR_SINGULAR) return;
+        const int64_t w = 2 * n - k;
+        for (int64_t q = (int64_t)blockIdx.x * blockDim.x + tid; q < n * w; q += (int64_t)gridDim.x * blockDim.x) {
+            const int64_t r = q / w, c = k + q % w;
+            const double f = fcol[r];
+            if (r != k && f != 0.0) M[r * 2 * n + c] -= f * M[k * 2 * n + c];
+        }
+        grid.sync();
     }
 }
 
@@ -1574,12 +1590,14 @@ int air_coarse_inverse(int64_t n, const int64_t *rp, const int32_t *ci, const do
     dense_scatter_kernel<<<air_counted(grid_for(n, 256)), 256, 0, s>>>(n, rp, ci, v, M);
     dense_absmax_kernel<<<air_counted(1), 1024, 0, s>>>(n, M, amax);
     AIR_LAUNCH();
-    unsigned eg = grid_for(n * 2 * n, 256, 152 * 8);
-    for (int64_t k = 0; k < n; ++k) {
-        gj_pivot_kernel<<<air_counted(1), 1024, 0, s>>>(n, k, M, fcol, amax, d_err);
-        gj_eliminate_kernel<<<air_counted(eg), 256, 0, s>>>(n, k, M, fcol, d_err);
-    }
-    AIR_LAUNCH();
+    int dev = 0, nsm = 0, per_sm = 0;
+    AIR_CUDA(cudaGetDevice(&dev));
+    AIR_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    AIR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gj_coop_kernel, 512, 0));
+    if (per_sm < 1) return AIR_ERR_CUDA;
+    int blocks = nsm;   // one co-resident block per SM
+    void *args[] = {(void *)&n, (void *)&M, (void *)&fcol, (void *)&amax, (void *)&d_err};
+    AIR_CUDA(cudaLaunchCooperativeKernel((const void *)gj_coop_kernel, dim3(air_counted(blocks).x), dim3(512), args, 0, s));
     dense_extract_kernel<<<air_counted(grid_for(n * n, 256)), 256, 0, s>>>(n, M, inv);
     AIR_LAUNCH();
     return AIR_OK;

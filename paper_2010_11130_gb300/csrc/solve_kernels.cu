@@ -13,6 +13,8 @@
 
 #include <type_traits>
 
+#include <cuda_bf16.h>
+
 #include "air_internal.cuh"
 
 namespace {
@@ -32,6 +34,11 @@ template <>
 struct Acc<double> { using type = double; };
 template <>
 struct Acc<float> { using type = float; };
+
+template <typename A, typename TV>
+__device__ __forceinline__ A to_acc(TV v) { return (A)v; }
+template <>
+__device__ __forceinline__ float to_acc<float, __nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
 
 template <int VL, typename A>
 __device__ __forceinline__ A seg_sum(A s) {
@@ -59,6 +66,7 @@ struct RowArgs {
     const TX *b;        // SpMV: optional (y = b - A x); Jacobi: right-hand side
     const TX *dinv;     // Jacobi: 1 / a_ii
     const int32_t *rows;  // Jacobi: the rows of the relaxed point set (ascending); n = their count
+    const TX *diag;       // if set, the stored values hold no diagonal: a_ii x_i is added from here
     TX omega;
 };
 
@@ -84,11 +92,13 @@ __global__ void __launch_bounds__(256) row_kernel(RowArgs<TV, TX> a) {
                 const int64_t e = rs + lane + (int64_t)u * VL;
                 const bool ok = e < re;
                 cols[u] = ok ? __ldg(a.ci + e) : 0;
-                vals[u] = ok ? __ldg(a.v + e) : (TV)0;
+                vals[u] = ok ? a.v[e] : (TV)0;
             }
 #pragma unroll
-            for (int u = 0; u < U; ++u) acc += (A)vals[u] * (A)__ldg(a.x + cols[u]);
-            for (int64_t e = rs + lane + (int64_t)U * VL; e < re; e += VL) acc += (A)a.v[e] * (A)a.x[a.ci[e]];
+            for (int u = 0; u < U; ++u) acc += to_acc<A, TV>(vals[u]) * (A)__ldg(a.x + cols[u]);
+            for (int64_t e = rs + lane + (int64_t)U * VL; e < re; e += VL)
+                acc += to_acc<A, TV>(a.v[e]) * (A)a.x[a.ci[e]];
+            if (a.diag && lane == 0) acc += (A)a.diag[row] * (A)a.x[row];
         }
         acc = seg_sum<VL, A>(acc);
         if (lane == 0 && valid) {
@@ -134,6 +144,19 @@ __global__ void dense_gemv_kernel(int64_t n, const T *__restrict__ Ci, const T *
 __global__ void d2f_kernel(const double *in, float *out, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         out[i] = (float)in[i];
+}
+
+// BF16 copy of CSR values with the diagonal entries set to zero (the
+// diagonal is kept separately in FP32); diag32 may be NULL (rectangular R).
+__global__ void d2bf_offdiag_kernel(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
+                                    __nv_bfloat16 *out, float *diag32) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
+            bool d = diag32 && ci[k] == i;
+            out[k] = __double2bfloat16(d ? 0.0 : v[k]);
+            if (d) diag32[i] = (float)v[k];
+        }
+    }
 }
 
 __global__ void f2d_kernel(const float *in, double *out, int64_t n) {
@@ -336,41 +359,40 @@ void spmv_dispatch(int64_t n, int64_t nnz, int32_t maxrow, const int64_t *rp, co
 
 // One Jacobi sweep over the point set `which` (0 = F, 1 = C), in place on x:
 // new values of the set's rows go to tmp, then are scattered back.
-template <typename T>
-void jacobi_dispatch(const AirLevel &L, const T *v, const T *dinv, int which, T omega, const T *b, T *x, T *tmp,
-                     cudaStream_t s) {
+template <typename TV, typename T>
+void jacobi_dispatch(const AirLevel &L, const TV *v, const T *diag, const T *dinv, int which, T omega, const T *b,
+                     T *x, T *tmp, cudaStream_t s) {
     const int32_t *rows = which ? L.crows : L.frows;
     int64_t m = which ? L.nc : L.nf;
     if (m == 0) return;
-    RowArgs<T, T> a{};
+    RowArgs<TV, T> a{};
     a.n = m; a.rp = L.rp; a.ci = L.ci; a.v = v; a.x = x; a.y = tmp; a.b = b; a.dinv = dinv; a.rows = rows;
+    a.diag = diag;
     a.omega = omega;
     int64_t nnz_set = L.n > 0 ? (int64_t)((double)L.nnz * (double)m / (double)L.n) : 0;
-    row_dispatch<T, T, ROW_JACOBI>(a, nnz_set, L.maxrow, s);
+    row_dispatch<TV, T, ROW_JACOBI>(a, nnz_set, L.maxrow, s);
     scatter_kernel<T><<<air_counted(grid_cap(m, 256)), 256, 0, s>>>(m, rows, tmp, x);
 }
 
-template <typename T>
-const T *lvl_vals(const AirLevel &L);
-template <>
-const double *lvl_vals<double>(const AirLevel &L) { return L.v; }
-template <>
-const float *lvl_vals<float>(const AirLevel &L) { return L.v32; }
-template <typename T>
-const T *lvl_dinv(const AirLevel &L);
-template <>
-const double *lvl_dinv<double>(const AirLevel &L) { return L.dinv; }
-template <>
-const float *lvl_dinv<float>(const AirLevel &L) { return L.dinv32; }
-template <typename T>
-const T *lvl_rvals(const AirLevel &L);
-template <>
-const double *lvl_rvals<double>(const AirLevel &L) { return L.rv; }
-template <>
-const float *lvl_rvals<float>(const AirLevel &L) { return L.rv32; }
+// Stored values of A_l / R_l in the storage type TV, the separate FP32
+// diagonal (BF16 storage only), and 1/a_ii in the vector type T.
+template <typename TV> const TV *lvl_vals(const AirLevel &L);
+template <> const double *lvl_vals<double>(const AirLevel &L) { return L.v; }
+template <> const float *lvl_vals<float>(const AirLevel &L) { return L.v32; }
+template <> const __nv_bfloat16 *lvl_vals<__nv_bfloat16>(const AirLevel &L) { return (const __nv_bfloat16 *)L.v16; }
+template <typename TV> const TV *lvl_rvals(const AirLevel &L);
+template <> const double *lvl_rvals<double>(const AirLevel &L) { return L.rv; }
+template <> const float *lvl_rvals<float>(const AirLevel &L) { return L.rv32; }
+template <> const __nv_bfloat16 *lvl_rvals<__nv_bfloat16>(const AirLevel &L) { return (const __nv_bfloat16 *)L.rv16; }
+template <typename T> const T *lvl_dinv(const AirLevel &L);
+template <> const double *lvl_dinv<double>(const AirLevel &L) { return L.dinv; }
+template <> const float *lvl_dinv<float>(const AirLevel &L) { return L.dinv32; }
+template <typename TV> const float *lvl_diag(const AirLevel &L) { return nullptr; }
+template <> const float *lvl_diag<__nv_bfloat16>(const AirLevel &L) { return L.diag32; }
 
-// V-cycle in precision T.  b0: finest right-hand side, x0: finest output.
-template <typename T>
+// V-cycle with values stored as TV and vectors in T.  b0: finest right-hand
+// side, x0: finest output.
+template <typename TV, typename T>
 int vcycle_t(const air_hierarchy *H, const T *b0, T *x0, cudaStream_t s) {
     int L = H->nlev;
     const char *relax = H->opt.relax;
@@ -380,8 +402,8 @@ int vcycle_t(const air_hierarchy *H, const T *b0, T *x0, cudaStream_t s) {
     for (int l = 0; l + 1 < L; ++l) {
         const AirLevel &A = H->lev[l];
         const T *bl = l == 0 ? b0 : (const T *)A.b;
-        spmv_dispatch<T, T>(A.nc, A.nnz_r, A.maxrow_r, A.rrp, A.rci, lvl_rvals<T>(A), bl, (T *)H->lev[l + 1].b,
-                            nullptr, s);
+        spmv_dispatch<TV, T>(A.nc, A.nnz_r, A.maxrow_r, A.rrp, A.rci, lvl_rvals<TV>(A), bl, (T *)H->lev[l + 1].b,
+                             nullptr, s);
     }
     // coarsest: x = A_L^{-1} b
     {
@@ -401,11 +423,12 @@ int vcycle_t(const air_hierarchy *H, const T *b0, T *x0, cudaStream_t s) {
         const T *xc = (const T *)H->lev[l + 1].x;
         // x = P x_c, then the sweeps in place
         interp_kernel<T><<<air_counted(grid_cap(A.n, 256)), 256, 0, s>>>(A.n, A.pcol, xc, out);
-        const T *v = lvl_vals<T>(A);
+        const TV *v = lvl_vals<TV>(A);
+        const T *diag = (const T *)lvl_diag<TV>(A);
         const T *dinv = lvl_dinv<T>(A);
         for (int q = 0; q < ns; ++q) {
             int which = relax[q] == 'C' ? 1 : 0;
-            jacobi_dispatch<T>(A, v, dinv, which, omega, bl, out, alt, s);
+            jacobi_dispatch<TV, T>(A, v, diag, dinv, which, omega, bl, out, alt, s);
         }
     }
     AIR_LAUNCH();
@@ -425,7 +448,7 @@ int air_spmv_f64(int64_t n, const int64_t *rp, const int32_t *ci, const double *
 // The V-cycle body (from the finest-level buffers lev[0].b to lev[0].x) is
 // captured once into a CUDA graph on a private stream and replayed on the
 // caller's stream; only the conversion in and out of lev[0] runs outside it.
-template <typename T>
+template <typename TV, typename T>
 int vcycle_graph(air_hierarchy *H, cudaStream_t s) {
     const AirLevel &L0 = H->lev[0];
     if (!H->vgraph && !H->vgraph_failed) {
@@ -435,7 +458,7 @@ int vcycle_graph(air_hierarchy *H, cudaStream_t s) {
         unsigned long long c0 = air_launch_counter_add(0);
         cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            int st = vcycle_t<T>(H, (const T *)L0.b, (T *)L0.x, cs);
+            int st = vcycle_t<TV, T>(H, (const T *)L0.b, (T *)L0.x, cs);
             e = cudaStreamEndCapture(cs, &g);
             if (st != AIR_OK && e == cudaSuccess) e = cudaErrorUnknown;
         }
@@ -457,28 +480,38 @@ int vcycle_graph(air_hierarchy *H, cudaStream_t s) {
         air_launch_counter_add((unsigned long long)H->vgraph_kernels);
         return AIR_OK;
     }
-    return vcycle_t<T>(H, (const T *)L0.b, (T *)L0.x, s);
+    return vcycle_t<TV, T>(H, (const T *)L0.b, (T *)L0.x, s);
 }
 
 int air_vcycle_run(const air_hierarchy *Hc, const double *b, double *x, cudaStream_t s, int use_graph) {
     air_hierarchy *H = const_cast<air_hierarchy *>(Hc);
     const AirLevel &L0 = H->lev[0];
     if (H->opt.precision == AIR_PREC_F64) {
-        if (!use_graph) return vcycle_t<double>(H, b, x, s);
+        if (!use_graph) return vcycle_t<double, double>(H, b, x, s);
         AIR_CUDA(cudaMemcpyAsync(L0.b, b, (size_t)L0.n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-        AIR_TRY(vcycle_graph<double>(H, s));
+        AIR_TRY((vcycle_graph<double, double>(H, s)));
         AIR_CUDA(cudaMemcpyAsync(x, L0.x, (size_t)L0.n * sizeof(double), cudaMemcpyDeviceToDevice, s));
         return AIR_OK;
     }
     float *b32 = (float *)L0.b, *x32 = (float *)L0.x;
     d2f_kernel<<<air_counted(grid_cap(L0.n, 256)), 256, 0, s>>>(b, b32, L0.n);
     AIR_LAUNCH();
+    const bool bf16 = H->opt.precision == AIR_PREC_BF16;
     if (use_graph) {
-        AIR_TRY(vcycle_graph<float>(H, s));
+        if (bf16) AIR_TRY((vcycle_graph<__nv_bfloat16, float>(H, s)));
+        else AIR_TRY((vcycle_graph<float, float>(H, s)));
     } else {
-        AIR_TRY(vcycle_t<float>(H, b32, x32, s));
+        if (bf16) AIR_TRY((vcycle_t<__nv_bfloat16, float>(H, b32, x32, s)));
+        else AIR_TRY((vcycle_t<float, float>(H, b32, x32, s)));
     }
     f2d_kernel<<<air_counted(grid_cap(L0.n, 256)), 256, 0, s>>>(x32, x, L0.n);
+    AIR_LAUNCH();
+    return AIR_OK;
+}
+
+int air_cast_bf16(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, void *out16, float *diag32,
+                  cudaStream_t s) {
+    d2bf_offdiag_kernel<<<air_counted(grid_cap(n, 256)), 256, 0, s>>>(n, rp, ci, v, (__nv_bfloat16 *)out16, diag32);
     AIR_LAUNCH();
     return AIR_OK;
 }

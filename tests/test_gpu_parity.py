@@ -22,6 +22,10 @@ VCYCLE_RTOL = 1e-10
 # ~5 levels x (restriction + 3 sweeps) with |R| row sums O(10) the relative
 # deviation of one V-cycle from the FP64 one stays below ~1e-4.
 VCYCLE_F32_RTOL = 1e-4
+# BF16 off-diagonals (unit roundoff 2^-9 ~ 2e-3 per stored value, diagonals
+# and vectors FP32): the same ~10 rounded passes bound one V-cycle's relative
+# deviation by ~2e-2; 5e-2 leaves room for cancellation in the coarse rows.
+VCYCLE_BF16_RTOL = 5e-2
 
 
 def _cases():
@@ -113,6 +117,33 @@ def test_vcycle_f32_within_derived_tolerance(name):
     torch.cuda.synchronize()
     xo = O.vcycle(s.rhs)
     assert np.linalg.norm(x.cpu().numpy() - xo) <= VCYCLE_F32_RTOL * np.linalg.norm(xo)
+
+
+@pytest.mark.parametrize("name", ["st1d_n32_p1", "st2d_n6_p2_nu1e-6"])
+def test_vcycle_bf16_within_derived_tolerance(name):
+    s = _system(name)
+    A16 = air.CSR.from_host(s.row_ptr, s.col, s.val)
+    H16 = air.setup(A16, theta=0.25, max_coarse=100, precision=2)
+    O = oracle.setup(s.row_ptr, s.col, s.val, theta=0.25, max_coarse=100)
+    x = H16.vcycle(torch.from_numpy(np.ascontiguousarray(s.rhs)).cuda())
+    torch.cuda.synchronize()
+    xo = O.vcycle(s.rhs)
+    assert np.linalg.norm(x.cpu().numpy() - xo) <= VCYCLE_BF16_RTOL * np.linalg.norm(xo)
+
+
+@pytest.mark.parametrize("name", ["st1d_n32_p1", "st2d_n6_p2_nu1e-6"])
+def test_fgmres_bf16_hierarchy_reaches_f64_accuracy(name):
+    s = _system(name)
+    A = air.CSR.from_host(s.row_ptr, s.col, s.val)
+    H = air.setup(A, theta=0.25, max_coarse=100, precision=2)
+    b = torch.from_numpy(np.ascontiguousarray(s.rhs)).cuda()
+    x, info = air.gmres_solve(A, H, b, rtol=1e-10)
+    torch.cuda.synchronize()
+    O = oracle.setup(s.row_ptr, s.col, s.val, theta=0.25, max_coarse=100)
+    xo, ito, _, _, _ = oracle.gmres(s.row_ptr, s.col, s.val, O, s.rhs, rtol=1e-10)
+    assert info.status == 0 and info.relres <= 1e-10
+    assert info.iters <= ito + 10
+    assert np.linalg.norm(x.cpu().numpy() - xo) <= 1e-8 * np.linalg.norm(xo)
 
 
 @pytest.mark.parametrize("name", list(_cases().keys()))
