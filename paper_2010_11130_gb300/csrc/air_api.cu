@@ -55,11 +55,14 @@ void free_level(AirLevel &L) {
         dfree(L.v);
     }
     L.rp = nullptr; L.ci = nullptr; L.v = nullptr;
-    dfree(L.v32); dfree(L.dinv); dfree(L.dinv32); dfree(L.v16); dfree(L.diag32); dfree(L.rv16);
+    dfree(L.dinv); dfree(L.dinv32); dfree(L.diag32);
     dfree(L.srp); dfree(L.sci);
     dfree(L.cf); dfree(L.cid); dfree(L.crows); dfree(L.frows);
-    dfree(L.rrp); dfree(L.rci); dfree(L.rv); dfree(L.rv32);
+    dfree(L.rrp); dfree(L.rci); dfree(L.rv);
     dfree(L.pcol);
+    air_free_sell(L.sset[0]);
+    air_free_sell(L.sset[1]);
+    air_free_sell(L.sr);
     dfree(L.b); dfree(L.x); dfree(L.x2);
 }
 
@@ -308,25 +311,21 @@ int setup_impl(const air_csr *A, const air_options *opt, cudaStream_t s, air_hie
             if (f32) AIR_TRY(dalloc(&L.dinv32, L.n));
             AIR_TRY(air_diag_inverse(L.n, L.rp, L.ci, L.v, L.dinv, L.dinv32, s));
             if (bf16) {
-                uint16_t *v16 = nullptr, *r16 = nullptr;
-                AIR_TRY(dalloc(&v16, L.nnz));
                 AIR_TRY(dalloc(&L.diag32, L.n));
-                AIR_TRY(air_cast_bf16(L.n, L.rp, L.ci, L.v, v16, L.diag32, s));
-                AIR_TRY(dalloc(&r16, L.nnz_r));
-                AIR_TRY(air_cast_bf16(L.nc, L.rrp, L.rci, L.rv, r16, nullptr, s));
-                L.v16 = v16;
-                L.rv16 = r16;
-            } else if (f32) {
-                AIR_TRY(dalloc(&L.v32, L.nnz));
-                AIR_TRY(air_cast_d2f(L.v, L.v32, L.nnz, s));
-                AIR_TRY(dalloc(&L.rv32, L.nnz_r));
-                AIR_TRY(air_cast_d2f(L.rv, L.rv32, L.nnz_r, s));
+                AIR_TRY(air_cast_bf16(L.n, L.rp, L.ci, L.v, nullptr, L.diag32, s));
             }
+            AIR_TRY(air_build_sell(L.nf, L.frows, L.rp, L.ci, L.v, opt->precision, bf16, &L.sset[0], s));
+            AIR_TRY(air_build_sell(L.nc, L.crows, L.rp, L.ci, L.v, opt->precision, bf16, &L.sset[1], s));
+            AIR_TRY(air_build_sell(L.nc, nullptr, L.rrp, L.rci, L.rv, opt->precision, 0, &L.sr, s));
         }
         size_t es = f32 ? sizeof(float) : sizeof(double);
         AIR_CUDA(cudaMalloc(&L.b, (size_t)(L.n > 0 ? L.n : 1) * es));
         AIR_CUDA(cudaMalloc(&L.x, (size_t)(L.n > 0 ? L.n : 1) * es));
         AIR_CUDA(cudaMalloc(&L.x2, (size_t)(L.n > 0 ? L.n : 1) * es));
+    }
+    {
+        AirLevel &L0 = H->lev[0];
+        AIR_TRY(air_build_sell(L0.n, nullptr, L0.rp, L0.ci, L0.v, AIR_PREC_F64, 0, &H->a0, s));
     }
     if (f32) {
         AIR_TRY(dalloc(&H->cinv32, H->nco * H->nco));
@@ -389,7 +388,7 @@ int gmres_impl(const AirLevel &A0, const air_hierarchy *Hc, const double *b, dou
     int it = 0;
     for (;;) {
         // r = b - A x into V_0 and its norm
-        AIR_TRY(air_spmv_f64(n, A0.rp, A0.ci, A0.v, x, H->V, b, s, A0.nnz, A0.maxrow));
+        AIR_TRY(air_sell_spmv_f64(H->a0, x, H->V, b, s));
         AIR_TRY(norm2(n, H->V, H->partials, nblk, sc + 3, s));
         AIR_CUDA(cudaMemcpyAsync(H->h_est + 3, sc + 3, sizeof(double), cudaMemcpyDeviceToHost, s));
         AIR_CUDA(cudaStreamSynchronize(s));
@@ -405,7 +404,7 @@ int gmres_impl(const AirLevel &A0, const air_hierarchy *Hc, const double *b, dou
             double *vj = H->V + (int64_t)j * n, *zj = H->Z + (int64_t)j * n, *w = H->V + (int64_t)(j + 1) * n;
             AIR_TRY(air_vcycle_run(H, vj, zj, s));
             info->vcycles++;
-            AIR_TRY(air_spmv_f64(n, A0.rp, A0.ci, A0.v, zj, w, nullptr, s, A0.nnz, A0.maxrow));
+            AIR_TRY(air_sell_spmv_f64(H->a0, zj, w, nullptr, s));
             // classical Gram-Schmidt, twice
             AIR_TRY(air_dot_partials(n, H->V, n, j + 1, w, H->partials, nblk, s));
             AIR_TRY(air_reduce_partials(j + 1, H->partials, nblk, h1, s));
@@ -570,6 +569,7 @@ void air_free(air_hierarchy *H) {
     if (cur != H->dev) cudaSetDevice(H->dev);
     cudaDeviceSynchronize();
     for (int l = 0; l < AIR_MAX_LEVELS; ++l) free_level(H->lev[l]);
+    air_free_sell(H->a0);
     if (H->vgraph) cudaGraphExecDestroy(H->vgraph);
     H->vgraph = nullptr;
     dfree(H->cinv);

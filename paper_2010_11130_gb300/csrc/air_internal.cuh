@@ -41,6 +41,20 @@ inline dim3 air_counted(dim3 g) {
 #define AIR_DEVERR_CSR 2
 #define AIR_DEVERR_SINGULAR 4
 
+// SELL-32 storage of a set of CSR rows: slice s holds rows 32s .. 32s+31 of
+// the set (in the order of `rows`); entry k of the slice's lane l sits at
+// ptr[s] + 32 k + l.  A slice is as wide as its longest row; shorter rows are
+// padded with zero values (column = the row itself).  Values are in the
+// V-cycle's storage type.
+struct Sell {
+    int64_t m = 0;              // rows
+    int32_t *rows = nullptr;    // pos -> row id (rows sorted by length inside windows of 1024)
+    int64_t *ptr = nullptr;     // m / 32 + 1 slice offsets
+    int32_t *ci = nullptr;
+    void *v = nullptr;
+    int64_t stored = 0;         // entries including padding
+};
+
 struct AirLevel {
     int64_t n = 0, nnz = 0;
     int32_t maxrow = 0, maxrow_r = 0; // longest row of A_l and of R_l
@@ -48,8 +62,6 @@ struct AirLevel {
     const int32_t *ci = nullptr;
     const double *v = nullptr;
     int owns_A = 0;
-    float *v32 = nullptr;             // F32 copy of A_l values
-    void *v16 = nullptr;              // BF16 copy of A_l off-diagonal values (diagonal zeroed)
     float *diag32 = nullptr;          // a_ii in FP32 (BF16 storage)
     double *dinv = nullptr;           // 1 / a_ii
     float *dinv32 = nullptr;
@@ -69,12 +81,15 @@ struct AirLevel {
     int64_t *rrp = nullptr;
     int32_t *rci = nullptr;
     double *rv = nullptr;
-    float *rv32 = nullptr;
-    void *rv16 = nullptr;
+
     int64_t n_singular = 0;
     int32_t max_m = 0;
     // one-point interpolation
     int32_t *pcol = nullptr;
+    // SELL-32 copies for the V-cycle: the rows of A_l split by point set
+    // (0 = F, 1 = C) for the relaxation sweeps, and R_l for the restriction
+    Sell sset[2];
+    Sell sr;
     // V-cycle work vectors (precision of the hierarchy)
     void *b = nullptr, *x = nullptr, *x2 = nullptr;
 };
@@ -91,6 +106,8 @@ struct air_hierarchy {
     // device scalars and scratch
     int *d_err = nullptr;
     unsigned long long *d_stats = nullptr;   // first-pass counters: picks, search iterations, slow picks
+    // SELL-32 FP64 copy of the finest operator for the GMRES matrix products
+    Sell a0;
     // V-cycle body captured as a CUDA graph on first use
     cudaGraphExec_t vgraph = nullptr;
     int vgraph_failed = 0;
@@ -148,6 +165,10 @@ int air_point_list(int64_t n, const int8_t *cf, int which, int32_t *list, int64_
 int air_cast_d2f(const double *in, float *out, int64_t n, cudaStream_t s);
 int air_cast_bf16(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, void *out16, float *diag32,
                   cudaStream_t s);
+int air_build_sell(int64_t m, const int32_t *rows, const int64_t *rp, const int32_t *ci, const double *v,
+                   int precision, int zero_diag, Sell *out, cudaStream_t s);
+void air_free_sell(Sell &S);
+int air_sell_spmv_f64(const Sell &S, const double *x, double *y, const double *b, cudaStream_t s);
 int air_diag_inverse(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, double *dinv,
                      float *dinv32, cudaStream_t s);
 

@@ -153,10 +153,150 @@ __global__ void d2bf_offdiag_kernel(int64_t n, const int64_t *rp, const int32_t 
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
             bool d = diag32 && ci[k] == i;
-            out[k] = __double2bfloat16(d ? 0.0 : v[k]);
+            if (out) out[k] = __double2bfloat16(d ? 0.0 : v[k]);
             if (d) diag32[i] = (float)v[k];
         }
     }
+}
+
+// -------------------------------------------------------------- SELL-32
+// sigma-sorting: inside each window of 1024 rows, order the rows by
+// decreasing length (ties by position) so each 32-row slice is nearly
+// uniform and carries little padding.
+constexpr int SIGMA = 1024;
+
+__global__ void __launch_bounds__(SIGMA / 2) sell_sort_kernel(int64_t m, const int32_t *rows, const int64_t *rp,
+                                                              int32_t *out) {
+    __shared__ unsigned long long key[SIGMA];
+    const int64_t w0 = (int64_t)blockIdx.x * SIGMA;
+    for (int t = threadIdx.x; t < SIGMA; t += blockDim.x) {
+        const int64_t p = w0 + t;
+        if (p < m) {
+            const int64_t r = rows ? rows[p] : p;
+            const unsigned len = (unsigned)(rp[r + 1] - rp[r]);
+            key[t] = ((unsigned long long)(0xffffffffu - len) << 32) | (unsigned)t;   // longest first
+        } else {
+            key[t] = ~0ull;
+        }
+    }
+    __syncthreads();
+    for (int size = 2; size <= SIGMA; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int idx = threadIdx.x; idx < SIGMA / 2; idx += blockDim.x) {
+                const int a = 2 * stride * (idx / stride) + (idx % stride), b = a + stride;
+                const bool up = (a & size) == 0;
+                const unsigned long long ka = key[a], kb = key[b];
+                if ((ka > kb) == up) { key[a] = kb; key[b] = ka; }
+            }
+            __syncthreads();
+        }
+    for (int t = threadIdx.x; t < SIGMA; t += blockDim.x) {
+        const int64_t p = w0 + t;
+        if (p < m) {
+            const int64_t src = w0 + (int64_t)(key[t] & 0xffffffffu);
+            out[p] = rows ? rows[src] : (int32_t)src;
+        }
+    }
+}
+
+__global__ void sell_width_kernel(int64_t m, const int32_t *rows, const int64_t *rp, int32_t *wid) {
+    const int64_t ns = (m + 31) / 32;
+    for (int64_t sl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; sl < ns; sl += (int64_t)gridDim.x * blockDim.x) {
+        int32_t w = 0;
+        for (int64_t p = sl * 32; p < m && p < sl * 32 + 32; ++p) {
+            const int64_t r = rows[p];
+            w = max(w, (int32_t)(rp[r + 1] - rp[r]));
+        }
+        wid[sl] = w * 32;
+    }
+}
+
+template <typename TV, bool ZERO_DIAG>
+__global__ void sell_fill_kernel(int64_t m, const int32_t *rows, const int64_t *rp, const int32_t *ci,
+                                 const double *v, const int64_t *ptr, int32_t *sci, TV *sv) {
+    const int64_t ns32 = ((m + 31) / 32) * 32;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < ns32; p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t sl = p >> 5, l = p & 31;
+        const int64_t base = ptr[sl], w = (ptr[sl + 1] - base) >> 5;
+        if (p < m) {
+            const int64_t r = rows[p];
+            const int64_t b = rp[r], len = rp[r + 1] - b;
+            for (int64_t k = 0; k < w; ++k) {
+                const int64_t dst = base + 32 * k + l;
+                if (k < len) {
+                    const int32_t c = ci[b + k];
+                    sci[dst] = c;
+                    sv[dst] = (TV)((ZERO_DIAG && c == r) ? 0.0 : v[b + k]);
+                } else {
+                    sci[dst] = (int32_t)r;
+                    sv[dst] = (TV)0.0;
+                }
+            }
+        } else {
+            for (int64_t k = 0; k < w; ++k) {   // lanes past the last row: harmless zeros
+                sci[base + 32 * k + l] = 0;
+                sv[base + 32 * k + l] = (TV)0.0;
+            }
+        }
+    }
+}
+
+template <typename TV, typename TX>
+struct SellArgs {
+    int64_t m;
+    const int64_t *ptr;
+    const int32_t *ci;
+    const TV *v;
+    const int32_t *rows;   // pos -> row id of the vectors
+    const TX *x;
+    TX *y;                 // SpMV: y[row]; Jacobi: y[pos] (compact, scattered afterwards)
+    const TX *b;
+    const TX *dinv;
+    const TX *diag;        // FP32 diagonal when the stored values hold none
+    TX omega;
+};
+
+// One thread per row: entry k of the 32 rows of a slice is one coalesced
+// load; UN entries are loaded before their x gathers.
+template <int UN, typename TV, typename TX, int MODE>
+__global__ void __launch_bounds__(256) sell_kernel(SellArgs<TV, TX> a) {
+    using A = typename Acc<TX>::type;
+    const int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (pos >= a.m) return;
+    const int64_t sl = pos >> 5;
+    const int l = (int)(pos & 31);
+    const int64_t base = a.ptr[sl];
+    const int w = (int)((a.ptr[sl + 1] - base) >> 5);
+    const int32_t *cp = a.ci + base + l;
+    const TV *vp = a.v + base + l;
+    A acc = 0;
+    int k = 0;
+    for (; k + UN <= w; k += UN) {
+        int32_t c[UN];
+        TV vv[UN];
+#pragma unroll
+        for (int u = 0; u < UN; ++u) {
+            c[u] = __ldg(cp + 32 * (k + u));
+            vv[u] = vp[32 * (k + u)];
+        }
+#pragma unroll
+        for (int u = 0; u < UN; ++u) acc += to_acc<A, TV>(vv[u]) * (A)__ldg(a.x + c[u]);
+    }
+    for (; k < w; ++k) acc += to_acc<A, TV>(vp[32 * k]) * (A)__ldg(a.x + cp[32 * k]);
+    const int64_t row = a.rows[pos];
+    if (MODE == ROW_SPMV) {
+        a.y[row] = a.b ? (TX)((A)a.b[row] - acc) : (TX)acc;
+    } else {
+        if (a.diag) acc += (A)a.diag[row] * (A)a.x[row];
+        a.y[pos] = (TX)(a.x[row] + a.omega * ((TX)((A)a.b[row] - acc)) * a.dinv[row]);
+    }
+}
+
+template <typename TV, typename TX, int MODE>
+void sell_launch(const SellArgs<TV, TX> &a, cudaStream_t s) {
+    if (a.m <= 0) return;
+    unsigned g = (unsigned)((a.m + 255) / 256);
+    sell_kernel<8, TV, TX, MODE><<<air_counted(g), 256, 0, s>>>(a);
 }
 
 __global__ void f2d_kernel(const float *in, double *out, int64_t n) {
@@ -360,30 +500,19 @@ void spmv_dispatch(int64_t n, int64_t nnz, int32_t maxrow, const int64_t *rp, co
 // One Jacobi sweep over the point set `which` (0 = F, 1 = C), in place on x:
 // new values of the set's rows go to tmp, then are scattered back.
 template <typename TV, typename T>
-void jacobi_dispatch(const AirLevel &L, const TV *v, const T *diag, const T *dinv, int which, T omega, const T *b,
-                     T *x, T *tmp, cudaStream_t s) {
-    const int32_t *rows = which ? L.crows : L.frows;
-    int64_t m = which ? L.nc : L.nf;
-    if (m == 0) return;
-    RowArgs<TV, T> a{};
-    a.n = m; a.rp = L.rp; a.ci = L.ci; a.v = v; a.x = x; a.y = tmp; a.b = b; a.dinv = dinv; a.rows = rows;
-    a.diag = diag;
-    a.omega = omega;
-    int64_t nnz_set = L.n > 0 ? (int64_t)((double)L.nnz * (double)m / (double)L.n) : 0;
-    row_dispatch<TV, T, ROW_JACOBI>(a, nnz_set, L.maxrow, s);
-    scatter_kernel<T><<<air_counted(grid_cap(m, 256)), 256, 0, s>>>(m, rows, tmp, x);
+void jacobi_dispatch(const AirLevel &L, const T *diag, const T *dinv, int which, T omega, const T *b, T *x, T *tmp,
+                     cudaStream_t s) {
+    const Sell &S = L.sset[which];
+    if (S.m == 0) return;
+    SellArgs<TV, T> a{};
+    a.m = S.m; a.ptr = S.ptr; a.ci = S.ci; a.v = (const TV *)S.v; a.rows = S.rows;
+    a.x = x; a.y = tmp; a.b = b; a.dinv = dinv; a.diag = diag; a.omega = omega;
+    sell_launch<TV, T, ROW_JACOBI>(a, s);
+    scatter_kernel<T><<<air_counted(grid_cap(S.m, 256)), 256, 0, s>>>(S.m, S.rows, tmp, x);
 }
 
-// Stored values of A_l / R_l in the storage type TV, the separate FP32
-// diagonal (BF16 storage only), and 1/a_ii in the vector type T.
-template <typename TV> const TV *lvl_vals(const AirLevel &L);
-template <> const double *lvl_vals<double>(const AirLevel &L) { return L.v; }
-template <> const float *lvl_vals<float>(const AirLevel &L) { return L.v32; }
-template <> const __nv_bfloat16 *lvl_vals<__nv_bfloat16>(const AirLevel &L) { return (const __nv_bfloat16 *)L.v16; }
-template <typename TV> const TV *lvl_rvals(const AirLevel &L);
-template <> const double *lvl_rvals<double>(const AirLevel &L) { return L.rv; }
-template <> const float *lvl_rvals<float>(const AirLevel &L) { return L.rv32; }
-template <> const __nv_bfloat16 *lvl_rvals<__nv_bfloat16>(const AirLevel &L) { return (const __nv_bfloat16 *)L.rv16; }
+// The separate FP32 diagonal (BF16 storage only) and 1/a_ii in the vector
+// type T.
 template <typename T> const T *lvl_dinv(const AirLevel &L);
 template <> const double *lvl_dinv<double>(const AirLevel &L) { return L.dinv; }
 template <> const float *lvl_dinv<float>(const AirLevel &L) { return L.dinv32; }
@@ -402,8 +531,10 @@ int vcycle_t(const air_hierarchy *H, const T *b0, T *x0, cudaStream_t s) {
     for (int l = 0; l + 1 < L; ++l) {
         const AirLevel &A = H->lev[l];
         const T *bl = l == 0 ? b0 : (const T *)A.b;
-        spmv_dispatch<TV, T>(A.nc, A.nnz_r, A.maxrow_r, A.rrp, A.rci, lvl_rvals<TV>(A), bl, (T *)H->lev[l + 1].b,
-                             nullptr, s);
+        SellArgs<TV, T> ra{};
+        ra.m = A.sr.m; ra.ptr = A.sr.ptr; ra.ci = A.sr.ci; ra.v = (const TV *)A.sr.v; ra.rows = A.sr.rows;
+        ra.x = bl; ra.y = (T *)H->lev[l + 1].b;
+        sell_launch<TV, T, ROW_SPMV>(ra, s);
     }
     // coarsest: x = A_L^{-1} b
     {
@@ -423,12 +554,11 @@ int vcycle_t(const air_hierarchy *H, const T *b0, T *x0, cudaStream_t s) {
         const T *xc = (const T *)H->lev[l + 1].x;
         // x = P x_c, then the sweeps in place
         interp_kernel<T><<<air_counted(grid_cap(A.n, 256)), 256, 0, s>>>(A.n, A.pcol, xc, out);
-        const TV *v = lvl_vals<TV>(A);
         const T *diag = (const T *)lvl_diag<TV>(A);
         const T *dinv = lvl_dinv<T>(A);
         for (int q = 0; q < ns; ++q) {
             int which = relax[q] == 'C' ? 1 : 0;
-            jacobi_dispatch<TV, T>(A, v, diag, dinv, which, omega, bl, out, alt, s);
+            jacobi_dispatch<TV, T>(A, diag, dinv, which, omega, bl, out, alt, s);
         }
     }
     AIR_LAUNCH();
@@ -505,6 +635,64 @@ int air_vcycle_run(const air_hierarchy *Hc, const double *b, double *x, cudaStre
         else AIR_TRY((vcycle_t<float, float>(H, b32, x32, s)));
     }
     f2d_kernel<<<air_counted(grid_cap(L0.n, 256)), 256, 0, s>>>(x32, x, L0.n);
+    AIR_LAUNCH();
+    return AIR_OK;
+}
+
+int air_build_sell(int64_t m, const int32_t *rows_in, const int64_t *rp, const int32_t *ci, const double *v,
+                   int precision, int zero_diag, Sell *out, cudaStream_t s) {
+    air_free_sell(*out);
+    out->m = m;
+    const int64_t ns = (m + 31) / 32;
+    AIR_CUDA(cudaMalloc(&out->rows, (size_t)(m > 0 ? m : 1) * sizeof(int32_t)));
+    if (m > 0) {
+        sell_sort_kernel<<<air_counted((unsigned)((m + SIGMA - 1) / SIGMA)), SIGMA / 2, 0, s>>>(m, rows_in, rp,
+                                                                                              out->rows);
+        AIR_LAUNCH();
+    }
+    const int32_t *rows = out->rows;
+    int32_t *wid = nullptr;
+    AIR_CUDA(cudaMalloc(&out->ptr, (size_t)(ns + 1) * sizeof(int64_t)));
+    AIR_CUDA(cudaMallocAsync(&wid, (size_t)(ns > 0 ? ns : 1) * sizeof(int32_t), s));
+    sell_width_kernel<<<air_counted(grid_cap(ns, 256)), 256, 0, s>>>(m, rows, rp, wid);
+    AIR_LAUNCH();
+    AIR_TRY(air_exclusive_scan_i32(wid, out->ptr, ns, s));
+    AIR_CUDA(cudaMemcpyAsync(&out->stored, out->ptr + ns, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    AIR_CUDA(cudaStreamSynchronize(s));
+    cudaFreeAsync(wid, s);
+    const int64_t cnt = out->stored > 0 ? out->stored : 1;
+    const size_t vb = precision == AIR_PREC_F64 ? 8 : (precision == AIR_PREC_F32 ? 4 : 2);
+    AIR_CUDA(cudaMalloc(&out->ci, (size_t)cnt * sizeof(int32_t)));
+    AIR_CUDA(cudaMalloc(&out->v, (size_t)cnt * vb));
+    unsigned g = grid_cap(ns * 32, 256, 152 * 32);
+    if (precision == AIR_PREC_F64)
+        sell_fill_kernel<double, false><<<air_counted(g), 256, 0, s>>>(m, rows, rp, ci, v, out->ptr, out->ci,
+                                                                       (double *)out->v);
+    else if (precision == AIR_PREC_F32)
+        sell_fill_kernel<float, false><<<air_counted(g), 256, 0, s>>>(m, rows, rp, ci, v, out->ptr, out->ci,
+                                                                      (float *)out->v);
+    else if (zero_diag)
+        sell_fill_kernel<__nv_bfloat16, true><<<air_counted(g), 256, 0, s>>>(m, rows, rp, ci, v, out->ptr, out->ci,
+                                                                             (__nv_bfloat16 *)out->v);
+    else
+        sell_fill_kernel<__nv_bfloat16, false><<<air_counted(g), 256, 0, s>>>(m, rows, rp, ci, v, out->ptr, out->ci,
+                                                                              (__nv_bfloat16 *)out->v);
+    AIR_LAUNCH();
+    return AIR_OK;
+}
+
+void air_free_sell(Sell &S) {
+    if (S.rows) cudaFree(S.rows);
+    if (S.ptr) cudaFree(S.ptr);
+    if (S.ci) cudaFree(S.ci);
+    if (S.v) cudaFree(S.v);
+    S = Sell();
+}
+
+int air_sell_spmv_f64(const Sell &S, const double *x, double *y, const double *b, cudaStream_t s) {
+    SellArgs<double, double> a{};
+    a.m = S.m; a.ptr = S.ptr; a.ci = S.ci; a.v = (const double *)S.v; a.rows = S.rows; a.x = x; a.y = y; a.b = b;
+    sell_launch<double, double, ROW_SPMV>(a, s);
     AIR_LAUNCH();
     return AIR_OK;
 }
