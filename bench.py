@@ -392,7 +392,7 @@ def run_ours(args):
                           "frac": sb / t_spmv / 1e9 / gbs_peak, "algorithmic_bytes": sb, "launch_s": t_spmv},
         "breakdown": breakdown,
         "dominant_kernel": {
-            "kernel": "rs3_warp_kernel (sequential first-pass C/F splitting, one warp per level)",
+            "kernel": "rs5_warp_kernel (sequential first-pass C/F splitting, one warp per level)",
             "bound": "latency (one dependent chain of picks; no HBM or ALU roofline applies)",
             "time_s": breakdown["f32"]["setup_phase_ms"]["splitting"] / 1e3,
             "share_of_step": breakdown["f32"]["setup_phase_ms"]["splitting"] / 1e3 / (ms32 / 1e3)},

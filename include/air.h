@@ -154,9 +154,11 @@ int air_gmres_solve_noalloc(const air_csr *A, const air_hierarchy *H, const doub
 /* Device time of air_setup's phases in milliseconds, summed over levels:
  * ms[0] strength, [1] transpose, [2] C/F splitting, [3] l-AIR restriction,
  * [4] one-point P, [5] Galerkin RAP, [6] coarsest inverse, [7] diagonals,
- * precision copies and vectors; then counters of the C/F splitting kernel:
- * ms[8] picks, [9] search iterations, [10] picks that took the general
- * (long-list) path.  Copies min(count, 11) values.  Measured
+ * precision copies and vectors; then counters of the C/F splitting kernel
+ * (filled by the default cursor kernel, zero for the other variants):
+ * ms[8] picks, [9] cursor refills (a bucket's cached 512-point line ran
+ * empty and the global bitmaps were searched), [10] bitmap lines read by
+ * those searches.  Copies min(count, 11) values.  Measured
  * with CUDA events on the setup stream; the paper reports only wall-clock
  * stage totals (Section 5.1: setup, assembly, solve, reconstruction). */
 int air_setup_timings(const air_hierarchy *H, double *ms, int count);

@@ -178,7 +178,7 @@ class Hierarchy:
         return self._h
 
     PHASES = ("strength", "transpose", "splitting", "lair", "onepoint_P", "rap", "coarsest", "other",
-              "split_picks", "split_search_iters", "split_slow_picks")
+              "split_picks", "split_refills", "split_lines_searched")
 
     def setup_timings(self) -> dict:
         """Device milliseconds per setup phase (summed over levels)."""

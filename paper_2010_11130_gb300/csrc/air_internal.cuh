@@ -143,6 +143,10 @@ int air_transpose_pattern(int64_t n, int64_t nnz, const int64_t *srp, const int3
 int air_rs_first_pass(int64_t n, const int64_t *srp, const int32_t *sci, const int64_t *strp,
                       const int32_t *stci, int32_t max_st, int32_t max_s, int8_t *cf, int *d_err, int cached,
                       unsigned long long *stats, cudaStream_t s);
+// first_pass.cu: the cursor first pass (AIR_ERR_UNSUPPORTED: outside its limits, nothing launched)
+int air_rs_first_pass_cursor(int64_t n, const int64_t *srp, const int32_t *sci, const int64_t *strp,
+                             const int32_t *stci, int32_t max_st, int8_t *cf, int *d_err,
+                             unsigned long long *stats, cudaStream_t s);
 int air_coarse_ids(int64_t n, const int8_t *cf, int32_t *cid, int32_t *crows, int64_t *work, int64_t *nc,
                    cudaStream_t s);
 int air_lair_counts(int64_t nc, const int32_t *crows, const int64_t *srp, const int32_t *sci, const int8_t *cf,

@@ -1434,6 +1434,11 @@ static int rs_first_pass_v3(int64_t n, const int64_t *srp, const int32_t *sci, c
 int air_rs_first_pass(int64_t n, const int64_t *srp, const int32_t *sci, const int64_t *strp, const int32_t *stci,
                       int32_t max_st, int32_t max_s, int8_t *cf, int *d_err, int cached,
                       unsigned long long *stats, cudaStream_t s) {
+    if (cached == 4) {
+        const int r = air_rs_first_pass_cursor(n, srp, sci, strp, stci, max_st, cf, d_err, stats, s);
+        if (r != AIR_ERR_UNSUPPORTED) return r;
+        cached = 2;
+    }
     if (cached == 3 && 2 * max_st + 1 <= 125)
         return rs_first_pass_v4(n, srp, sci, strp, stci, max_st, max_s, cf, d_err, stats, s);
     if (cached >= 2 && 2 * max_st + 1 <= 125)
