@@ -242,8 +242,8 @@ int setup_impl(const air_csr *A, const air_options *opt, cudaStream_t s, air_hie
     AIR_CUDA(cudaGetDevice(&H->dev));
     AIR_TRY(dalloc(&H->d_err, 1));
     AIR_CUDA(cudaMemsetAsync(H->d_err, 0, sizeof(int), s));
-    AIR_TRY(dalloc(&H->d_stats, 4));
-    AIR_CUDA(cudaMemsetAsync(H->d_stats, 0, 4 * sizeof(unsigned long long), s));
+    AIR_TRY(dalloc(&H->d_stats, 8));
+    AIR_CUDA(cudaMemsetAsync(H->d_stats, 0, 8 * sizeof(unsigned long long), s));
     AirLevel &L0 = H->lev[0];
     L0.n = A->n_rows;
     L0.nnz = A->nnz;

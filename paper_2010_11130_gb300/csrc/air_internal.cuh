@@ -105,7 +105,7 @@ struct air_hierarchy {
     float *cinv32 = nullptr;
     // device scalars and scratch
     int *d_err = nullptr;
-    unsigned long long *d_stats = nullptr;   // first-pass counters: picks, search iterations, slow picks
+    unsigned long long *d_stats = nullptr;   // 8 first-pass counters: picks, refills, lines searched, long lists, cursor moves
     // SELL-32 FP64 copy of the finest operator for the GMRES matrix products
     Sell a0;
     // V-cycle body captured as a CUDA graph on first use

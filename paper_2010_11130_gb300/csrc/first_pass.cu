@@ -6,16 +6,16 @@
 // C, its undecided strong dependants S^T_i become F, every undecided k in S_j
 // of a new F point j gains 1 and every undecided k in S_i loses 1.  Each pick
 // depends on the one before, so the whole pass runs on one warp; the kernel
-// below is built to keep the dependent chain of one pick to two memory round
-// trips:
+// below is built to keep the dependent chain of one pick short:
 //
-//  * each point's two-hop list (S^T_i, then S_j for each j in S^T_i, then S_i)
-//    sits in a fixed-size line of 32-bit entries (point index in the low 25
-//    bits, the role in the high 7), so a pick's whole list arrives in one
-//    coalesced load addressed by the point alone;
-//  * the measures of the listed points arrive in the second load; every
-//    consequence of the pick (new F points, summed measure changes) is then
-//    combined in registers and a shared-memory hash table;
+//  * each point's two-hop neighbourhood is stored once per distinct point, in
+//    a fixed-size block addressed by the point alone: the members of S^T_i
+//    first (in order), then every other point of some S_j (j in S^T_i) or of
+//    S_i, each with a bit mask of the S_j lists it belongs to and a flag for
+//    S_i.  One load brings a pick's neighbourhood, a second the measures of
+//    its points; with F_new the mask of the undecided members of S^T_i, a
+//    listed undecided point then changes by popc(mask & F_new) - [k in S_i],
+//    independently of every other listed point, so no combining is needed;
 //  * for every bucket (measure value) the block keeps its population and a
 //    cursor: a 512-point line below which the bucket has no members, with the
 //    exact contents of that line.  The pick's own changes keep populations and
@@ -32,26 +32,25 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int8_t M_F = -1, M_C = -2;          // measure codes of decided points
-constexpr uint32_t ROLE_SI = 126u, ROLE_J = 127u;
 constexpr int K_BITS = 25;
 constexpr uint32_t K_MASK = (1u << K_BITS) - 1u;
+constexpr uint32_t F_J = 1u << 25;             // entry is a member of S^T_i
+constexpr uint32_t F_SI = 1u << 26;            // entry is a member of S_i
 constexpr int NB_MAX = 128;                    // buckets; measures <= 124 fit int8
-constexpr int LINE = 128;                      // words per list line: header + 127 entries
+constexpr int BLK_E = 64;                      // positions per block: header + 63 entries
+constexpr int BLK_W = BLK_E + 2 * BLK_E;       // 32-bit words per block: entries, then 64-bit masks
 constexpr int EMAX = 1024;                     // positions per list (header + 1023 entries)
-constexpr int TS_BITS = 11;
-constexpr int TS = 1 << TS_BITS;               // hash slots, >= 2x the entries of one list
-constexpr int F_BIAS = 4096;                   // hash value of a point that becomes F (> 2 EMAX)
+constexpr int F_BIAS = 4096;                   // contribution of a point that becomes F (> 2 EMAX)
 constexpr int32_t CL_INF = 0x7fffffff;         // cursor of an empty bucket
-constexpr int OWNER = 4096;                    // slot code of the position that claimed the slot
-static_assert(OWNER >= TS && OWNER + TS <= 32767, "slot codes must fit int16");
 static_assert(F_BIAS > 2 * EMAX, "an F mark must dominate any sum of +-1 contributions");
 
 struct RS5Args {
     int32_t n;
     int nb;                    // buckets 0 .. nb-1 (bucket 0 is never stored)
-    const uint32_t *lines;     // n * LINE words
-    const int64_t *optr;       // start of each point's overflow entries (positions >= LINE)
-    const uint32_t *ovf;
+    const uint32_t *blocks;    // n * BLK_W words: [0] header, [1 + e] entry e (e < 63), masks at word 64 + 2 (1 + e)
+    const int64_t *optr;       // start of each point's overflow entries (e >= 63)
+    const uint32_t *ovf;       // overflow entries
+    const uint64_t *ovfm;      // overflow masks
     int8_t *lam;
     uint64_t *L0, *L1;         // nb * w0 leaf words, nb * w1 summary words
     const uint64_t *L2;        // nb * w2 second summary (initial copy)
@@ -79,6 +78,7 @@ __device__ __forceinline__ void red_and(uint64_t *p, uint64_t v) {
     atomicAnd((unsigned long long *)p, (unsigned long long)v);
 }
 
+// Upper bound on the distinct points of a neighbourhood: |S^T_i| + sum |S_j| + |S_i|.
 __global__ void list_count_kernel(int64_t n, const int64_t *srp, const int64_t *strp, const int32_t *stci,
                                   int32_t *cnt) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -91,33 +91,64 @@ __global__ void list_count_kernel(int64_t n, const int64_t *srp, const int64_t *
     }
 }
 
-// Line of point i: word 0 = entries | |S^T_i| << 11, word p = entry p - 1 for
-// p < LINE, the rest at ovf[optr[i] + p - LINE].  Roles: ROLE_J for S^T_i, t
-// (the position of j in S^T_i) for S_j, ROLE_SI for S_i.
-__global__ void list_fill_kernel(int64_t n, const int64_t *srp, const int32_t *sci, const int64_t *strp,
-                                 const int32_t *stci, const int64_t *optr, uint32_t *lines, uint32_t *ovf) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        uint32_t *line = lines + (size_t)i * LINE;
-        const int64_t o = optr[i];
-        int p = 1;
-        auto put = [&](uint32_t v) {
-            if (p < LINE) line[p] = v; else ovf[o + (p - LINE)] = v;
-            ++p;
-        };
-        for (int64_t q = strp[i]; q < strp[i + 1]; ++q) put((ROLE_J << K_BITS) | (uint32_t)stci[q]);
-        uint32_t t = 0;
-        for (int64_t q = strp[i]; q < strp[i + 1]; ++q, ++t) {
-            const int32_t j = stci[q];
-            for (int64_t r = srp[j]; r < srp[j + 1]; ++r) put((t << K_BITS) | (uint32_t)sci[r]);
-        }
-        for (int64_t r = srp[i]; r < srp[i + 1]; ++r) put((ROLE_SI << K_BITS) | (uint32_t)sci[r]);
-        line[0] = (uint32_t)(p - 1) | ((uint32_t)(strp[i + 1] - strp[i]) << 11);
-    }
-}
-
 __global__ void overflow_count_kernel(int64_t n, const int32_t *cnt, int32_t *ocnt) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        ocnt[i] = cnt[i] + 1 > LINE ? cnt[i] + 1 - LINE : 0;
+        ocnt[i] = cnt[i] + 1 > BLK_E ? cnt[i] + 1 - BLK_E : 0;
+}
+
+// Neighbourhood block of point i, one entry per distinct point other than i:
+// the members j_0, j_1, ... of S^T_i first (flag F_J), then the points of the
+// lists S_{j_t} (mask bit t) and of S_i (flag F_SI) in first-seen order.
+// Header: entries | |S^T_i| << 11.
+__global__ void list_fill_kernel(int64_t n, const int64_t *srp, const int32_t *sci, const int64_t *strp,
+                                 const int32_t *stci, const int64_t *optr, uint32_t *blocks, uint32_t *ovf,
+                                 uint64_t *ovfm) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t *blk = blocks + (size_t)i * BLK_W;
+        uint64_t *msk = (uint64_t *)(blk + BLK_E);
+        const int64_t o = optr[i];
+        auto ent = [&](int e) -> uint32_t & { return e < BLK_E - 1 ? blk[1 + e] : ovf[o + (e - (BLK_E - 1))]; };
+        auto mask = [&](int e) -> uint64_t & { return e < BLK_E - 1 ? msk[1 + e] : ovfm[o + (e - (BLK_E - 1))]; };
+        auto find = [&](int u, int32_t k) {
+            for (int e = 0; e < u; ++e)
+                if ((int32_t)(ent(e) & K_MASK) == k) return e;
+            return -1;
+        };
+        int u = 0;
+        for (int64_t q = strp[i]; q < strp[i + 1]; ++q) {
+            ent(u) = F_J | (uint32_t)stci[q];
+            mask(u) = 0ull;
+            ++u;
+        }
+        int t = 0;
+        for (int64_t q = strp[i]; q < strp[i + 1]; ++q, ++t) {
+            const int32_t j = stci[q];
+            for (int64_t r = srp[j]; r < srp[j + 1]; ++r) {
+                const int32_t k = sci[r];
+                if (k == (int32_t)i) continue;          // i itself becomes C
+                const int e = find(u, k);
+                if (e >= 0) {
+                    mask(e) |= 1ull << t;
+                } else {
+                    ent(u) = (uint32_t)k;
+                    mask(u) = 1ull << t;
+                    ++u;
+                }
+            }
+        }
+        for (int64_t r = srp[i]; r < srp[i + 1]; ++r) {
+            const int32_t k = sci[r];
+            const int e = find(u, k);
+            if (e >= 0) {
+                ent(e) |= F_SI;
+            } else {
+                ent(u) = F_SI | (uint32_t)k;
+                mask(u) = 0ull;
+                ++u;
+            }
+        }
+        blk[0] = (uint32_t)u | ((uint32_t)(strp[i + 1] - strp[i]) << 11);
+    }
 }
 
 // Measures, exact bitmaps at all three levels and bucket populations.
@@ -156,16 +187,10 @@ struct Shared {
     uint32_t *cv;     // NB_MAX * 16: contents of each bucket's cursor line (512 points)
     uint32_t *L2s;    // nb * s2 second-level summary bits (bit q: summary word q may be non-zero)
     int32_t *pop;     // NB_MAX bucket populations
-    int32_t *cl;      // NB_MAX cursor line (-1: not yet searched, CL_INF: empty bucket)
-    int32_t *cl2;     // NB_MAX shadow of cl collecting the lowest new line
-    int32_t *tk;      // TS hash keys (-1 empty)
-    int32_t *tv;      // TS hash values
-    uint32_t *sent;   // EMAX list entries of the current pick (position p = entry p - 1)
-    int32_t *rk;      // EMAX records: point, bucket left, bucket entered
+    int32_t *cl;      // NB_MAX cursor line (-1: not yet searched, CL_INF: never had a cursor)
+    int32_t *pl;      // NB_MAX lowest line of insertions below the cursor (CL_INF: none)
+    int32_t *rk;      // EMAX records of long lists: point, bucket left, bucket entered
     int8_t *rob, *rnb;
-    int8_t *slv;      // EMAX measures of the listed points at the start of the pick (-3: not live)
-    int16_t *sslot;   // EMAX hash slot of the position (+ OWNER when it owns the slot), -1 none
-    int8_t *jf;       // 64 new-F flags of the S^T_i entries
     int s2;           // 32-bit words of L2s per bucket
 };
 
@@ -175,8 +200,8 @@ __device__ __forceinline__ unsigned lanemask_lt() {
     return m;
 }
 
-__device__ __forceinline__ void prefetch_line(const uint32_t *p) {
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "r"(LINE * 4u)
+__device__ __forceinline__ void prefetch_block(const uint32_t *p) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "r"(BLK_W * 4u)
                  : "memory");
 }
 
@@ -229,7 +254,7 @@ __device__ bool rs5_refill(const RS5Args &a, const Shared &s, int b, int64_t *st
                 s.cv[b * 16 + 2 * lane] = (uint32_t)lw;
                 s.cv[b * 16 + 2 * lane + 1] = (uint32_t)(lw >> 32);
             }
-            if (lane == 0) { s.cl[b] = line; s.cl2[b] = line; }
+            if (lane == 0) { s.cl[b] = line; s.pl[b] = CL_INF; }
             __syncwarp();
             return true;
         }
@@ -248,16 +273,10 @@ __global__ void __launch_bounds__(32) rs5_warp_kernel(RS5Args a) {
     s.L2s = s.cv + NB_MAX * 16;
     s.pop = (int32_t *)(s.L2s + (int64_t)a.nb * s.s2);
     s.cl = s.pop + NB_MAX;
-    s.cl2 = s.cl + NB_MAX;
-    s.tk = s.cl2 + NB_MAX;
-    s.tv = s.tk + TS;
-    s.sent = (uint32_t *)(s.tv + TS);
-    s.rk = (int32_t *)(s.sent + EMAX);
-    s.sslot = (int16_t *)(s.rk + EMAX + 32);
-    s.rob = (int8_t *)(s.sslot + EMAX);
-    s.rnb = s.rob + EMAX + 32;
-    s.slv = s.rnb + EMAX + 32;
-    s.jf = s.slv + EMAX;
+    s.pl = s.cl + NB_MAX;
+    s.rk = s.pl + NB_MAX;
+    s.rob = (int8_t *)(s.rk + EMAX);
+    s.rnb = s.rob + EMAX;
     const int lane = threadIdx.x & 31;
     const uint32_t *L2g = (const uint32_t *)a.L2;
     for (int64_t t = lane; t < (int64_t)a.nb * s.s2; t += 32) s.L2s[t] = L2g[t];
@@ -267,20 +286,33 @@ __global__ void __launch_bounds__(32) rs5_warp_kernel(RS5Args a) {
         const int32_t p = (b >= 1 && b < a.nb) ? a.pop0[b] : 0;
         s.pop[b] = p;
         s.cl[b] = p > 0 ? -1 : CL_INF;
-        s.cl2[b] = s.cl[b];
+        s.pl[b] = CL_INF;
         if (p > 0) top = b;
     }
-    for (int t = lane; t < TS; t += 32) { s.tk[t] = -1; s.tv[t] = 0; }
     top = (int)__reduce_max_sync(FULL, (unsigned)top);
     __syncwarp();
     int64_t steps = 0;
-    unsigned long long picks = 0, refills = 0, visits = 0, longs = 0;
+    unsigned long long picks = 0, refills = 0, visits = 0, longs = 0, moves = 0;
     bool failed = false;
     while (true) {
         // ---- the pick: lowest member of the highest non-empty bucket
         while (top >= 1 && s.pop[top] == 0) --top;
         if (top < 1) break;
         const int B = top;
+        if (s.pl[B] < s.cl[B]) {
+            // insertions below the cursor: move it down to the lowest of them and
+            // read that line (the bucket has no members below it)
+            const int32_t line = s.pl[B];
+            const uint64_t lw = lane < 8 ? __ldcg((const unsigned long long *)&a.L0[(int64_t)B * a.w0 + line * 8 + lane]) : 0ull;
+            if (lane < 8) {
+                s.cv[B * 16 + 2 * lane] = (uint32_t)lw;
+                s.cv[B * 16 + 2 * lane + 1] = (uint32_t)(lw >> 32);
+            }
+            __syncwarp();
+            if (lane == 0) { s.cl[B] = line; s.pl[B] = CL_INF; }
+            ++moves;
+            __syncwarp();
+        }
         uint32_t wv = lane < 16 ? s.cv[B * 16 + lane] : 0u;
         unsigned bal = __ballot_sync(FULL, wv != 0u);
         if (bal == 0u) {
@@ -295,48 +327,44 @@ __global__ void __launch_bounds__(32) rs5_warp_kernel(RS5Args a) {
         const int32_t lbase = s.cl[B] * 512;
         const int32_t i = lbase + sw * 32 + (__ffs(word) - 1);
         if (++picks > (unsigned long long)a.n || i >= a.n) { failed = true; break; }
-        // the next members of the same line are the likely next picks: warm their lists in L2
+        // the next members of the same line are the likely next picks: warm their blocks in L2
         {
             const uint32_t rest = lane == sw ? (word & (word - 1u)) : wv;
             const unsigned nz = __ballot_sync(FULL, rest != 0u);
             if (rest != 0u && __popc(nz & lanemask_lt()) < 3)
-                prefetch_line(a.lines + (size_t)(lbase + lane * 32 + (__ffs(rest) - 1)) * LINE);
+                prefetch_block(a.blocks + (size_t)(lbase + lane * 32 + (__ffs(rest) - 1)) * BLK_W);
         }
 
-        // ---- round trip 1: the two-hop list of i
-        const uint32_t *line = a.lines + (size_t)i * LINE;
-        uint32_t ent[LINE / 32];
-#pragma unroll
-        for (int r = 0; r < LINE / 32; ++r) ent[r] = __ldcg(line + lane + 32 * r);
-        const uint32_t hdr = __shfl_sync(FULL, ent[0], 0);
-        const int np = (int)(hdr & 2047u) + 1;          // positions: header + entries
-        const int nj = (int)((hdr >> 11) & 63u);
+        // ---- round trip 1: the neighbourhood of i (positions lane and lane + 32)
+        const uint32_t *blk = a.blocks + (size_t)i * BLK_W;
+        const uint64_t *bmk = (const uint64_t *)(blk + BLK_E);
+        const uint32_t e0 = __ldcg(blk + lane), e1 = __ldcg(blk + 32 + lane);
+        const uint64_t m0 = __ldcg((const unsigned long long *)bmk + lane);
+        const uint64_t m1 = __ldcg((const unsigned long long *)bmk + 32 + lane);
+        const uint32_t hdr = __shfl_sync(FULL, e0, 0);
+        const int np = (int)(hdr & 2047u) + 1;           // positions: header + entries
+        const int nj = (int)((hdr >> 11) & 63u);         // entries 0 .. nj-1 are S^T_i (positions 1 .. nj)
+        const bool two = np > 32;
 
         // ---- round trip 2: measures of the listed points
-        int lv[LINE / 32];
-#pragma unroll
-        for (int r = 0; r < LINE / 32; ++r) {
-            const int p = lane + 32 * r;
-            const int32_t k = (int32_t)(ent[r] & K_MASK);
-            lv[r] = (p >= 1 && p < np && k != i) ? (int)__ldcg(a.lam + k) : -3;
-        }
-        // Each changed point gets one record (point, bucket left, bucket entered;
-        // 0 = none): in a register of the owning lane when the list fits one
-        // position per lane, else in shared memory.
-        const bool fast = np <= 32;
-        int32_t fk = 0;
-        int fob = 0, fnb = 0;
-        int nrec = 0, vmax = 0;
+        const int32_t k0 = (int32_t)(e0 & K_MASK), k1 = (int32_t)(e1 & K_MASK);
+        const int l0 = (lane >= 1 && lane < np) ? (int)__ldcg(a.lam + k0) : -3;
+        const int l1 = (two && lane + 32 < np) ? (int)__ldcg(a.lam + k1) : -3;
+        // F_new: the undecided members of S^T_i, bit t for entry t
+        const unsigned f0 = __ballot_sync(FULL, lane >= 1 && lane <= nj && l0 >= 0);
+        const unsigned f1 = __ballot_sync(FULL, lane + 32 <= nj && l1 >= 0);
+        const uint64_t fnew = (uint64_t)(f0 >> 1) | ((uint64_t)f1 << 31);
+        int vmax = 0;
         bool bad = false;
-        // new state of a changed point from its measure l and summed contribution v
-        auto settle = [&](int32_t k, int l, int v, int &ob, int &nbk) {
+        // new state of a listed point from its measure l and its change c (F_BIAS: becomes F)
+        auto settle = [&](int32_t k, int l, int c, int &ob, int &nbk) {
             ob = 0;
             nbk = 0;
-            if (v >= F_BIAS / 2) {
+            if (c >= F_BIAS / 2) {
                 a.lam[k] = M_F;
                 ob = l >= 1 ? l : 0;
-            } else if (v != 0) {
-                int nv = l + v;
+            } else if (c != 0) {
+                int nv = l + c;
                 if (nv < 0 || nv >= a.nb) { bad = true; nv = 0; }   // cannot happen: 0 <= measure <= 2 max|S^T|
                 a.lam[k] = (int8_t)nv;
                 ob = l >= 1 ? l : 0;
@@ -347,165 +375,101 @@ __global__ void __launch_bounds__(32) rs5_warp_kernel(RS5Args a) {
                 red_xor(&a.L0[(int64_t)nbk * a.w0 + (k >> 6)], 1ull << (k & 63));
                 red_or(&a.L1[(int64_t)nbk * a.w1 + (k >> 12)], 1ull << ((k >> 6) & 63));
                 atomicOr(&s.L2s[(int64_t)nbk * s.s2 + (k >> 17)], 1u << ((k >> 12) & 31));
-                if (nbk > B) prefetch_line(a.lines + (size_t)k * LINE);   // a candidate for the next pick
+                if (nbk > B) prefetch_block(a.blocks + (size_t)k * BLK_W);   // a candidate for the next pick
             }
             vmax = max(vmax, nbk);
         };
-        if (fast) {
-            // one position per lane: combine duplicates with warp matching
-            const int32_t k = (int32_t)(ent[0] & K_MASK);
-            const uint32_t role = ent[0] >> K_BITS;
-            const int l = lv[0];
-            const bool newF = lane >= 1 && lane - 1 < nj && l >= 0;     // undecided members of S^T_i
-            const bool jnew = __shfl_sync(FULL, newF, role < ROLE_SI ? (int)(role + 1) & 31 : 0);
-            int contrib = 0;
-            if (l >= 0) contrib = (lane - 1 < nj) ? F_BIAS : (role == ROLE_SI ? -1 : (jnew ? 1 : 0));
-            // per-group sums from three full-warp ballots (a reduction over each
-            // match group would serialise over the distinct groups)
-            const unsigned m = __match_any_sync(FULL, contrib != 0 ? (uint32_t)k : (0x80000000u | (uint32_t)lane));
-            const unsigned bF = __ballot_sync(FULL, contrib == F_BIAS);
-            const unsigned bP = __ballot_sync(FULL, contrib == 1);
-            const unsigned bM = __ballot_sync(FULL, contrib == -1);
-            const int v = F_BIAS * __popc(bF & m) + __popc(bP & m) - __popc(bM & m);
-            if (contrib != 0 && lane == __ffs(m) - 1) {
-                fk = k;
-                settle(k, l, v, fob, fnb);
-            }
-            if (lane == 0) {                              // the header lane carries the pick's record
-                fk = i;
-                fob = B;
-                fnb = 0;
-            }
-        } else {
-#pragma unroll
-            for (int r = 0; r < LINE / 32; ++r) {
-                const int p = lane + 32 * r;
-                if (p < np) { s.sent[p] = ent[r]; s.slv[p] = (int8_t)lv[r]; }
-                if (p >= 1 && p - 1 < nj) s.jf[p - 1] = lv[r] >= 0 ? 1 : 0;   // new F points: undecided S^T_i
-            }
-            if (np > LINE) {                             // long list: the rest from the overflow area
-                ++longs;
-                const int64_t op = a.optr[i];
-                for (int p = LINE + lane; p < np; p += 32) {
-                    const uint32_t e = __ldcg(a.ovf + op + (p - LINE));
-                    const int32_t k = (int32_t)(e & K_MASK);
-                    s.sent[p] = e;
-                    s.slv[p] = (int8_t)(k != i ? (int)__ldcg(a.lam + k) : -3);
-                }
-            }
-            __syncwarp();
-            // contributions of every live entry, summed per point in the hash table
-            for (int p = lane; p < np; p += 32) {
-                int16_t sl = -1;
-                const int l = p >= 1 ? (int)s.slv[p] : -3;
-                if (l >= 0) {
-                    const uint32_t ev = s.sent[p];
-                    const uint32_t role = ev >> K_BITS;
-                    const int32_t k = (int32_t)(ev & K_MASK);
-                    const int contrib = (p - 1 < nj) ? F_BIAS : (role == ROLE_SI ? -1 : (s.jf[role] ? 1 : 0));
-                    if (contrib != 0) {
-                        int h = (int)(((uint32_t)k * 2654435761u) >> (32 - TS_BITS));
-                        bool own = false;
-                        for (int t = 0; t < TS; ++t) {
-                            const int old = atomicCAS(&s.tk[h], -1, k);
-                            if (old == -1) { own = true; break; }
-                            if (old == k) break;
-                            h = (h + 1) & (TS - 1);
-                        }
-                        atomicAdd(&s.tv[h], contrib);
-                        sl = (int16_t)(h + (own ? OWNER : 0));
-                    }
-                }
-                s.sslot[p] = sl;
-            }
-            __syncwarp();
-            // owners settle their point and append its record
-            for (int base = 0; base < np; base += 32) {
+        auto change = [&](uint32_t e, uint64_t m, int l, bool is_j) {
+            if (l < 0) return 0;
+            if (is_j) return F_BIAS;
+            return __popcll(m & fnew) - ((e & F_SI) ? 1 : 0);
+        };
+        // one record per changed point: two in registers per lane, the rest of a long list in shared memory
+        int32_t rk0 = k0, rk1 = k1;
+        int ob0, nb0, ob1 = 0, nb1 = 0;
+        settle(k0, l0, change(e0, m0, l0, lane <= nj), ob0, nb0);
+        if (two) settle(k1, l1, change(e1, m1, l1, lane + 32 <= nj), ob1, nb1);
+        if (lane == 0) {                                   // the header slot carries the pick's own record
+            rk0 = i;
+            ob0 = B;
+            nb0 = 0;
+            a.lam[i] = M_C;
+            red_xor(&a.L0[(int64_t)B * a.w0 + (i >> 6)], 1ull << (i & 63));
+        }
+        int nx = 0;
+        if (np > BLK_E) {                                  // long list: entries 63.. from the overflow area
+            ++longs;
+            const int64_t op = a.optr[i];
+            for (int base = BLK_E; base < np; base += 32) {
                 const int p = base + lane;
                 int ob = 0, nbk = 0;
                 int32_t k = 0;
-                const int sl = p < np ? (int)s.sslot[p] : -1;
-                if (sl >= OWNER) {
-                    const int h = sl - OWNER;
-                    const int v = s.tv[h];
-                    s.tk[h] = -1;
-                    s.tv[h] = 0;
-                    k = (int32_t)(s.sent[p] & K_MASK);
-                    settle(k, (int)s.slv[p], v, ob, nbk);
+                if (p < np) {
+                    const uint32_t e = __ldcg(a.ovf + op + (p - BLK_E));
+                    const uint64_t m = __ldcg((const unsigned long long *)a.ovfm + op + (p - BLK_E));
+                    k = (int32_t)(e & K_MASK);
+                    const int l = (int)__ldcg(a.lam + k);
+                    settle(k, l, change(e, m, l, false), ob, nbk);   // S^T_i has at most 62 members
                 }
                 const bool has = ob != 0 || nbk != 0;
                 const unsigned hb = __ballot_sync(FULL, has);
                 if (has) {
-                    const int q = nrec + __popc(hb & lanemask_lt());
+                    const int q = nx + __popc(hb & lanemask_lt());
                     s.rk[q] = k;
                     s.rob[q] = (int8_t)ob;
                     s.rnb[q] = (int8_t)nbk;
                 }
-                nrec += __popc(hb);
+                nx += __popc(hb);
             }
-            if (lane == 0) {                              // the pick's record
-                s.rk[nrec] = i;
-                s.rob[nrec] = (int8_t)B;
-                s.rnb[nrec] = 0;
-            }
-            ++nrec;
         }
         if (__any_sync(FULL, bad)) { failed = true; break; }
-        if (lane == 0) {                                  // the pick itself leaves bucket B
-            a.lam[i] = M_C;
-            red_xor(&a.L0[(int64_t)B * a.w0 + (i >> 6)], 1ull << (i & 63));
-        }
         __syncwarp();
         // visit every record of the pick
         auto each = [&](auto fn) {
-            if (fast) {
-                fn(fk, fob, fnb);
-            } else {
-                for (int q = lane; q < nrec; q += 32) fn(s.rk[q], (int)s.rob[q], (int)s.rnb[q]);
-            }
+            fn(rk0, ob0, nb0);
+            if (two) fn(rk1, ob1, nb1);
+            for (int q = lane; q < nx; q += 32) fn(s.rk[q], (int)s.rob[q], (int)s.rnb[q]);
         };
-        // cursors and populations.  A: removals (the fast path adds one
-        // population change per bucket, from warp matching)
-        if (fast) {
-            const unsigned m = __match_any_sync(FULL, fob ? (uint32_t)fob : (0x100u | (uint32_t)lane));
-            if (fob && lane == __ffs(m) - 1) atomicSub(&s.pop[fob], __popc(m));
+        // one population change per bucket and register round, from warp matching
+        // (lanes without a change share one key: match cost grows with the
+        // number of distinct keys).  Returns the population before the change
+        // to the group's leader.
+        auto add_pop = [&](int b, int sign) {
+            const unsigned m = __match_any_sync(FULL, (uint32_t)b);
+            int old = -1;
+            if (b && lane == __ffs(m) - 1) old = atomicAdd(&s.pop[b], sign * __popc(m));
+            return old + (b && lane == __ffs(m) - 1 ? sign * __popc(m) : 0);
+        };
+        // populations and cursors.  A change inside a bucket's cursor line
+        // toggles its bit (a removal clears a set bit, an insertion sets a clear
+        // one); an insertion below the cursor only lowers the pending line, which
+        // the next pick from that bucket reads from the leaf bitmap.  A bucket
+        // left empty forgets its cursor, so that its next members all count as
+        // insertions below it.  A: removals
+        {
+            auto forget = [&](int b) { s.cl[b] = CL_INF; s.pl[b] = CL_INF; };
+            if (add_pop(ob0, -1) == 0) forget(ob0);
+            if (two && add_pop(ob1, -1) == 0) forget(ob1);
+            for (int q = lane; q < nx; q += 32) {
+                const int ob = s.rob[q];
+                if (ob && atomicSub(&s.pop[ob], 1) == 1) forget(ob);
+            }
         }
         each([&](int32_t k, int ob, int) {
-            if (ob) {
-                if (!fast) atomicSub(&s.pop[ob], 1);
-                if ((k >> 9) == s.cl[ob]) atomicXor(&s.cv[ob * 16 + ((k >> 5) & 15)], 1u << (k & 31));
-            }
+            if (ob && (k >> 9) == s.cl[ob]) atomicXor(&s.cv[ob * 16 + ((k >> 5) & 15)], 1u << (k & 31));
         });
         __syncwarp();
-        // B: a bucket left empty forgets its cursor
-        each([&](int32_t, int ob, int) {
-            if (ob && s.pop[ob] == 0) { s.cl[ob] = CL_INF; s.cl2[ob] = CL_INF; }
-        });
-        __syncwarp();
-        // C: insertions; a point below a bucket's cursor pulls the cursor down
-        if (fast) {
-            const unsigned m = __match_any_sync(FULL, fnb ? (uint32_t)fnb : (0x100u | (uint32_t)lane));
-            if (fnb && lane == __ffs(m) - 1) atomicAdd(&s.pop[fnb], __popc(m));
-        }
+        // B: insertions
+        add_pop(nb0, 1);
+        if (two) add_pop(nb1, 1);
+        for (int q = lane; q < nx; q += 32)
+            if (s.rnb[q]) atomicAdd(&s.pop[s.rnb[q]], 1);
         each([&](int32_t k, int, int nbk) {
             if (nbk) {
-                if (!fast) atomicAdd(&s.pop[nbk], 1);
-                if ((k >> 9) < s.cl[nbk]) atomicMin(&s.cl2[nbk], k >> 9);
+                const int32_t L = k >> 9, c = s.cl[nbk];
+                if (L == c) atomicXor(&s.cv[nbk * 16 + ((k >> 5) & 15)], 1u << (k & 31));
+                else if (L < c) atomicMin(&s.pl[nbk], L);
             }
-        });
-        __syncwarp();
-        // D: a moved cursor starts from an empty line (the bucket had no members
-        // there); several records may move the same cursor, all to the same line
-        each([&](int32_t, int, int nbk) {
-            if (nbk && s.cl2[nbk] < s.cl[nbk]) {
-                for (int t = 0; t < 16; ++t) s.cv[nbk * 16 + t] = 0u;
-                s.cl[nbk] = s.cl2[nbk];
-            }
-        });
-        __syncwarp();
-        // E: insertions into the cursor line
-        each([&](int32_t k, int, int nbk) {
-            if (nbk && (k >> 9) == s.cl[nbk]) atomicOr(&s.cv[nbk * 16 + ((k >> 5) & 15)], 1u << (k & 31));
         });
         __syncwarp();
         vmax = (int)__reduce_max_sync(FULL, (unsigned)vmax);
@@ -517,6 +481,7 @@ __global__ void __launch_bounds__(32) rs5_warp_kernel(RS5Args a) {
         a.stats[1] += refills;
         a.stats[2] += visits;
         a.stats[3] += longs;
+        a.stats[4] += moves;
     }
 }
 
@@ -529,7 +494,7 @@ int air_rs_first_pass_cursor(int64_t n, const int64_t *srp, const int32_t *sci, 
                              const int32_t *stci, int32_t max_st, int8_t *cf, int *d_err,
                              unsigned long long *stats, cudaStream_t s) {
     const int nb = 2 * max_st + 1 < 2 ? 2 : 2 * max_st + 1;
-    if (n <= 0 || n >= (int64_t)1 << K_BITS || nb > 125) return AIR_ERR_UNSUPPORTED;
+    if (n <= 0 || n >= (int64_t)1 << K_BITS || nb > 125 || max_st > 62) return AIR_ERR_UNSUPPORTED;
     int32_t *cnt = nullptr, *dmax = nullptr;
     AIR_CUDA(cudaMallocAsync(&cnt, (size_t)n * sizeof(int32_t), s));
     AIR_CUDA(cudaMallocAsync(&dmax, sizeof(int32_t), s));
@@ -545,7 +510,7 @@ int air_rs_first_pass_cursor(int64_t n, const int64_t *srp, const int32_t *sci, 
         cudaFreeAsync(cnt, s);
         return AIR_ERR_UNSUPPORTED;
     }
-    // overflow area for lists longer than a line
+    // overflow area for neighbourhoods longer than a block (sized by the upper bound)
     int32_t *ocnt = nullptr;
     int64_t *optr = nullptr;
     AIR_CUDA(cudaMallocAsync(&ocnt, (size_t)n * sizeof(int32_t), s));
@@ -570,10 +535,13 @@ int air_rs_first_pass_cursor(int64_t n, const int64_t *srp, const int32_t *sci, 
     // empty line; stale bits come only from insertions (at most one per list
     // entry per pick)
     a.cap = 4 * (int64_t)n * (int64_t)EMAX + 4096;
-    uint32_t *lines = nullptr, *ovf = nullptr;
-    AIR_CUDA(cudaMallocAsync(&lines, (size_t)n * LINE * sizeof(uint32_t), s));
+    uint32_t *blocks = nullptr, *ovf = nullptr;
+    uint64_t *ovfm = nullptr;
+    AIR_CUDA(cudaMallocAsync(&blocks, (size_t)n * BLK_W * sizeof(uint32_t), s));
     AIR_CUDA(cudaMallocAsync(&ovf, (size_t)(novf > 0 ? novf : 1) * sizeof(uint32_t), s));
-    list_fill_kernel<<<air_counted(blocks_for(n, 256)), 256, 0, s>>>(n, srp, sci, strp, stci, optr, lines, ovf);
+    AIR_CUDA(cudaMallocAsync(&ovfm, (size_t)(novf > 0 ? novf : 1) * sizeof(uint64_t), s));
+    list_fill_kernel<<<air_counted(blocks_for(n, 256)), 256, 0, s>>>(n, srp, sci, strp, stci, optr, blocks, ovf,
+                                                                      ovfm);
     AIR_LAUNCH();
     const size_t words = (size_t)nb * (size_t)(a.w0 + a.w1 + a.w2);
     uint64_t *bits = nullptr;
@@ -589,15 +557,15 @@ int air_rs_first_pass_cursor(int64_t n, const int64_t *srp, const int32_t *sci, 
     uint64_t *L2 = a.L1 + (size_t)nb * a.w1;
     a.L2 = L2;
     a.lam = lam;
-    a.lines = lines;
+    a.blocks = blocks;
     a.optr = optr;
     a.ovf = ovf;
+    a.ovfm = ovfm;
     a.pop0 = pop;
     rs5_init_kernel<<<air_counted(blocks_for(n, 256)), 256, 0, s>>>(a, srp, strp, L2, pop);
     AIR_LAUNCH();
-    const size_t smem = (size_t)NB_MAX * 16 * 4 + (size_t)nb * 2 * a.w2 * 4 + 3 * NB_MAX * 4 + 2 * TS * 4 +
-                        (size_t)EMAX * 4 + (size_t)(EMAX + 32) * 4 + (size_t)EMAX * 2 + 2 * (size_t)(EMAX + 32) +
-                        (size_t)EMAX + 64;
+    const size_t smem = (size_t)NB_MAX * 16 * 4 + (size_t)nb * 2 * a.w2 * 4 + 3 * NB_MAX * 4 + (size_t)EMAX * 4 +
+                        2 * (size_t)EMAX + 64;
     int st = AIR_OK;
     if (smem > 200 * 1024) {
         st = AIR_ERR_UNSUPPORTED;
@@ -611,8 +579,9 @@ int air_rs_first_pass_cursor(int64_t n, const int64_t *srp, const int32_t *sci, 
     cudaFreeAsync(bits, s);
     cudaFreeAsync(pop, s);
     cudaFreeAsync(lam, s);
-    cudaFreeAsync(lines, s);
+    cudaFreeAsync(blocks, s);
     cudaFreeAsync(ovf, s);
+    cudaFreeAsync(ovfm, s);
     cudaFreeAsync(optr, s);
     return st;
 }
