@@ -121,6 +121,25 @@ int air_vcycle(const air_hierarchy *H, const double *b, double *x, void *stream)
 /* y = A x for device CSR A and device vectors.  Asynchronous. */
 int air_spmv(const air_csr *A, const double *x, double *y, void *stream);
 
+/* Adjoint support.  The paper solves only the forward system S Lambda = H
+ * (Section 2.5) and has no adjoint; these two calls serve the gradient of a
+ * loss L(u) through u = A^{-1} b: with lambda = A^{-T} dL/du (an l-AIR solve on
+ * the transpose, whose unit diagonal blocks and reversed upwind structure suit
+ * the same setup), dL/db = lambda and dL/da_ij = -lambda_i u_j.
+ *
+ * air_csr_transpose: A^T of a device CSR (n_rows x n_cols) into caller-owned
+ * device arrays row_ptr_t (n_cols + 1), col_t (nnz), val_t (nnz); columns
+ * ascending in every row, values moved bit for bit.  Returns
+ * AIR_ERR_CSR_MALFORMED if a column index is out of range, AIR_ERR_INVALID_ARG
+ * for a host CSR or NULL pointers.  Synchronises the stream once. */
+int air_csr_transpose(const air_csr *A, int64_t *row_ptr_t, int32_t *col_t, double *val_t, void *stream);
+
+/* out[e] = alpha * u[i] * w[j] for every stored entry e = (i, j) of the device
+ * CSR A (the gradient of L over A's values with alpha = -1, u = lambda,
+ * w = the forward solution).  out has nnz entries, device, caller-owned; an
+ * entry whose column is out of range gets NaN.  Asynchronous on the stream. */
+int air_csr_outer(const air_csr *A, const double *u, const double *w, double alpha, double *out, void *stream);
+
 /* Right-preconditioned flexible GMRES(restart) with classical Gram-Schmidt
  * applied twice, x0 = 0, until ||b - A x|| / ||b|| <= rtol (the paper's
  * Krylov method is BiCGSTAB; GMRES is named as an alternative in Section 5.1).

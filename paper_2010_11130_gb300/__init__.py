@@ -4,6 +4,6 @@ The compute path is libair.so (hand-written CUDA for sm_103a, C ABI in
 include/air.h); this package holds its sources, the in-tree build and the
 ctypes binding.
 """
-from .air import (CSR, AirError, Hierarchy, default_options, gmres_solve, lib, setup,  # noqa: F401
-                  spmv, status_string, kernel_launches)
+from .air import (CSR, AdjointSolver, AirError, Hierarchy, csr_outer, default_options,  # noqa: F401
+                  gmres_solve, kernel_launches, lib, setup, spmv, status_string, transpose)
 from .build import build  # noqa: F401

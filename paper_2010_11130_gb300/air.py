@@ -23,7 +23,8 @@ AIR_PREC_BF16 = 2
 
 EXPORTED = ["air_default_options", "air_setup", "air_vcycle", "air_spmv", "air_gmres_solve",
             "air_hierarchy_levels", "air_hierarchy_info", "air_hierarchy_export", "air_free",
-            "air_status_string", "air_kernel_launches", "air_gmres_solve_noalloc", "air_setup_timings"]
+            "air_status_string", "air_kernel_launches", "air_gmres_solve_noalloc", "air_setup_timings",
+            "air_csr_transpose", "air_csr_outer"]
 
 
 class air_csr(C.Structure):
@@ -96,6 +97,10 @@ def lib() -> C.CDLL:
     L.air_kernel_launches.restype = C.c_ulonglong
     L.air_status_string.argtypes = [C.c_int]
     L.air_status_string.restype = C.c_char_p
+    L.air_csr_transpose.argtypes = [C.POINTER(air_csr), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    L.air_csr_transpose.restype = C.c_int
+    L.air_csr_outer.argtypes = [C.POINTER(air_csr), C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p]
+    L.air_csr_outer.restype = C.c_int
     _lib = L
     return L
 
@@ -280,3 +285,95 @@ def gmres_solve_noalloc(A: CSR, H: Hierarchy, b, x, rtol: float = 1e-8, stream=N
                                        float(rtol), C.c_void_p(_stream(stream)), C.byref(inf))
     _check(st, "air_gmres_solve_noalloc")
     return x, inf
+
+
+# ------------------------------------------------------------------ adjoint
+def transpose(A: CSR, stream=None) -> CSR:
+    """air_csr_transpose: A^T of a square device CSR, columns ascending, values bit for bit."""
+    import torch
+    dev = A.val.device
+    rp = torch.empty(A.n + 1, dtype=torch.int64, device=dev)
+    ci = torch.empty(max(A.nnz, 1), dtype=torch.int32, device=dev)[:A.nnz]
+    v = torch.empty(max(A.nnz, 1), dtype=torch.float64, device=dev)[:A.nnz]
+    Ac = A.c()
+    _check(lib().air_csr_transpose(C.byref(Ac), C.c_void_p(rp.data_ptr()), C.c_void_p(ci.data_ptr()),
+                                   C.c_void_p(v.data_ptr()), C.c_void_p(_stream(stream))), "air_csr_transpose")
+    return CSR(rp, ci, v, A.n)
+
+
+def csr_outer(A: CSR, u, w, alpha: float = 1.0, out=None, stream=None):
+    """air_csr_outer: out[e] = alpha * u[i] * w[j] over the stored entries (i, j) of A."""
+    import torch
+    if out is None:
+        out = torch.empty(max(A.nnz, 1), dtype=torch.float64, device=A.val.device)[:A.nnz]
+    Ac = A.c()
+    _check(lib().air_csr_outer(C.byref(Ac), C.c_void_p(u.data_ptr()), C.c_void_p(w.data_ptr()), float(alpha),
+                               C.c_void_p(out.data_ptr()), C.c_void_p(_stream(stream))), "air_csr_outer")
+    return out
+
+
+_SOLVE_FN = None
+
+
+def _solve_fn():
+    """torch.autograd.Function of u = A^{-1} b (built on first use)."""
+    global _SOLVE_FN
+    if _SOLVE_FN is None:
+        import torch
+
+        class AirSolve(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, b, val, solver):
+                x, info = gmres_solve(solver.A, solver.H, b.detach().contiguous(), rtol=solver.rtol)
+                solver.info = info
+                if info.status != 0:
+                    raise AirError(info.status, "forward solve did not converge")
+                ctx.solver = solver
+                ctx.save_for_backward(x)
+                return x
+
+            @staticmethod
+            def backward(ctx, gx):
+                (x,) = ctx.saved_tensors
+                solver = ctx.solver
+                lam = solver.solve_adjoint(gx.contiguous())
+                gval = csr_outer(solver.A, lam, x, -1.0) if ctx.needs_input_grad[1] else None
+                return lam, gval, None
+
+        _SOLVE_FN = AirSolve
+    return _SOLVE_FN
+
+
+class AdjointSolver:
+    """Forward and adjoint l-AIR solves of one matrix A, differentiable.
+
+    solve(b) returns u = A^{-1} b as a torch tensor that autograd
+    differentiates: the backward pass solves A^T lambda = dL/du with a second
+    l-AIR hierarchy built on A^T (built on the first backward) and returns
+    dL/db = lambda and, when A.val requires grad, dL/dA.val = -lambda_i u_j on
+    the stored entries.  The hierarchies are built from A's values at
+    construction time; rebuild the solver after changing them.
+    """
+
+    def __init__(self, A: CSR, rtol: float = 1e-8, theta: float = 0.25, **opts):
+        self.A, self.rtol, self.theta, self.opts = A, rtol, theta, opts
+        self.H = setup(A, theta=theta, **opts)
+        self.At = self.Ht = None
+        self.info = self.info_adjoint = None
+
+    def adjoint_hierarchy(self):
+        if self.Ht is None:
+            self.At = transpose(self.A)
+            self.Ht = setup(self.At, theta=self.theta, **self.opts)
+        return self.At, self.Ht
+
+    def solve_adjoint(self, g):
+        At, Ht = self.adjoint_hierarchy()
+        lam, info = gmres_solve(At, Ht, g, rtol=self.rtol)
+        self.info_adjoint = info
+        if info.status != 0:
+            raise AirError(info.status, "adjoint solve did not converge")
+        return lam
+
+    def solve(self, b, val=None):
+        return _solve_fn().apply(b, self.A.val if val is None else val, self)

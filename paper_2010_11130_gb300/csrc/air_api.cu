@@ -494,6 +494,33 @@ int air_spmv(const air_csr *A, const double *x, double *y, void *stream) {
     return air_spmv_f64(A->n_rows, A->row_ptr, A->col, A->val, x, y, nullptr, (cudaStream_t)stream, A->nnz, 0);
 }
 
+int air_csr_transpose(const air_csr *A, int64_t *row_ptr_t, int32_t *col_t, double *val_t, void *stream) {
+    if (!A || !row_ptr_t || !A->on_device || A->n_rows < 0 || A->n_cols < 0 || A->nnz < 0 || !A->row_ptr)
+        return AIR_ERR_INVALID_ARG;
+    if (A->nnz > 0 && (!A->col || !A->val || !col_t || !val_t)) return AIR_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    int *d_err = nullptr;
+    AIR_CUDA(cudaMallocAsync(&d_err, sizeof(int), s));
+    AIR_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), s));
+    int st = air_csr_transpose_impl(A->n_rows, A->n_cols, A->nnz, A->row_ptr, A->col, A->val, row_ptr_t, col_t,
+                                    val_t, d_err, s);
+    int herr = 0;
+    if (st == AIR_OK) {
+        cudaError_t e = cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = AIR_ERR_CUDA;
+    }
+    cudaFreeAsync(d_err, s);
+    if (st == AIR_OK && herr) st = AIR_ERR_CSR_MALFORMED;
+    return st;
+}
+
+int air_csr_outer(const air_csr *A, const double *u, const double *w, double alpha, double *out, void *stream) {
+    if (!A || !A->on_device || A->n_rows < 0 || A->nnz < 0 || !A->row_ptr) return AIR_ERR_INVALID_ARG;
+    if (A->nnz > 0 && (!A->col || !u || !w || !out)) return AIR_ERR_INVALID_ARG;
+    return air_csr_outer_impl(A->n_rows, A->n_cols, A->row_ptr, A->col, u, w, alpha, out, (cudaStream_t)stream);
+}
+
 int air_gmres_solve(const air_csr *A, const air_hierarchy *H, const double *b, double *x, double rtol, void *stream,
                     air_solve_info *info) {
     if (!A || !H || !b || !x || !(rtol > 0.0) || A->n_rows != H->lev[0].n) return AIR_ERR_INVALID_ARG;

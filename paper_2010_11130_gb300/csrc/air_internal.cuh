@@ -159,6 +159,12 @@ int air_rap_terms(const AirLevel &L, int32_t *terms, cudaStream_t s);
 int air_coarse_inverse(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, double *inv,
                        double *work, int *d_err, cudaStream_t s);
 
+// adjoint.cu
+int air_csr_transpose_impl(int64_t n, int64_t ncols, int64_t nnz, const int64_t *rp, const int32_t *ci,
+                           const double *v, int64_t *rpt, int32_t *cit, double *vt, int *d_err, cudaStream_t s);
+int air_csr_outer_impl(int64_t n, int64_t ncols, const int64_t *rp, const int32_t *ci, const double *u,
+                       const double *w, double alpha, double *out, cudaStream_t s);
+
 // solve_kernels.cu
 // y = A x, or y = b - A x if b != NULL; nnz < 0 / maxrow <= 0 when unknown
 int air_spmv_f64(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, const double *x,
