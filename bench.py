@@ -52,6 +52,11 @@ def parse():
     ap.add_argument("--vcycles", type=int, default=20)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--workload", default="single", choices=["single", "batched"],
+                    help="batched: 16 independent uneven problems set up and solved at once")
+    ap.add_argument("--batch-count", type=int, default=16)
+    ap.add_argument("--batch-nmin", type=int, default=16)
+    ap.add_argument("--batch-nmax", type=int, default=48)
     return ap.parse_args()
 
 
@@ -405,10 +410,63 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_batched(args):
+    """Independent uneven problems (seeded recipe of sthdg.problems.batched_problems):
+    FP32 hierarchies built with air_setup_batch and solved with
+    air_gmres_solve_batch, against the same calls made one problem at a time."""
+    import torch
+    import paper_2010_11130_gb300 as air
+    from sthdg import assemble
+    from sthdg.problems import batched_problems
+    air.build()
+    t0 = time.perf_counter()
+    probs, _ = batched_problems(args.batch_count, (args.batch_nmin, args.batch_nmax))
+    sys_ = [assemble(p, workers=args.workers) for p in probs]
+    gen_s = time.perf_counter() - t0
+    As = [air.CSR.from_host(s.row_ptr, s.col, s.val) for s in sys_]
+    bs = [torch.from_numpy(np.ascontiguousarray(s.rhs)).cuda() for s in sys_]
+    air.setup(As[0], precision=1)                     # warm-up: module load, memory pools
+    torch.cuda.synchronize()
+
+    def batch_step():
+        Hs, st = air.setup_batch(As, precision=1)
+        assert all(x == 0 for x in st), st
+        xs, infos, st2 = air.gmres_solve_batch(As, Hs, bs, rtol=args.rtol)
+        assert all(x == 0 for x in st2), st2
+        return infos
+
+    def serial_step():
+        infos = []
+        for A, b in zip(As, bs):
+            H = air.setup(A, precision=1)
+            infos.append(air.gmres_solve(A, H, b, rtol=args.rtol)[1])
+        return infos
+
+    times = {}
+    for name, fn in (("batched", batch_step), ("one_at_a_time", serial_step)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        infos = fn()
+        torch.cuda.synchronize()
+        times[name] = time.perf_counter() - t0
+    out = {"metric": "batched AIR-GMRES time-to-1e-8 over independent problems (setup+solve s)",
+           "value": times["batched"], "unit": "s", "n_gpus": 1, "steps": 1, "warmup": 1,
+           "higher_is_better": False, "dtype": "f32 hierarchy / f64 Krylov", "data": "synthetic",
+           "config": {"workload": f"batched_{args.batch_count}_st2d_n{args.batch_nmin}-{args.batch_nmax}",
+                      "problems": [{"n": p.n, "p": p.p, "nu": p.nu, "unknowns": s.n} for p, s in zip(probs, sys_)],
+                      "unknowns_total": int(sum(s.n for s in sys_))},
+           "one_at_a_time_s": times["one_at_a_time"],
+           "speedup": times["one_at_a_time"] / times["batched"],
+           "iters": [i.iters for i in infos], "generate_s": gen_s}
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
     else:
         run_ours(args)
 

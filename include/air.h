@@ -121,6 +121,23 @@ int air_vcycle(const air_hierarchy *H, const double *b, double *x, void *stream)
 /* y = A x for device CSR A and device vectors.  Asynchronous. */
 int air_spmv(const air_csr *A, const double *x, double *y, void *stream);
 
+/* Independent problems at once.  The paper solves one system at a time;
+ * these run count independent setups (or solves) concurrently, one host
+ * thread and one stream per problem (streams[k], or a library-created stream
+ * when streams is NULL or streams[k] is NULL), and return when all are done.
+ * Each problem's result is exactly that of the single-problem call.  A is an
+ * array of count air_csr; out / H / b / x / info / status are arrays of
+ * count.  status[k] (if status is not NULL) receives problem k's status; the
+ * return value is the first negative status, else AIR_OK (a solve that stops
+ * at max_iter reports AIR_NOT_CONVERGED in status[k] and info[k] only).  A
+ * hierarchy may appear only once in a solve batch (AIR_ERR_INVALID_ARG):
+ * its Krylov workspace serves one solve at a time. */
+int air_setup_batch(int count, const air_csr *A, double theta, int distance, const air_options *opt,
+                    void *const *streams, air_hierarchy **out, int *status);
+int air_gmres_solve_batch(int count, const air_csr *A, const air_hierarchy *const *H, const double *const *b,
+                          double *const *x, double rtol, void *const *streams, air_solve_info *info,
+                          int *status);
+
 /* Adjoint support.  The paper solves only the forward system S Lambda = H
  * (Section 2.5) and has no adjoint; these two calls serve the gradient of a
  * loss L(u) through u = A^{-1} b: with lambda = A^{-T} dL/du (an l-AIR solve on

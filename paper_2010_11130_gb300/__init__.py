@@ -5,5 +5,6 @@ include/air.h); this package holds its sources, the in-tree build and the
 ctypes binding.
 """
 from .air import (CSR, AdjointSolver, AirError, Hierarchy, csr_outer, default_options,  # noqa: F401
-                  gmres_solve, kernel_launches, lib, setup, spmv, status_string, transpose)
+                  gmres_solve, gmres_solve_batch, kernel_launches, lib, setup, setup_batch, spmv,
+                  status_string, transpose)
 from .build import build  # noqa: F401

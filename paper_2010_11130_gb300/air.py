@@ -24,7 +24,7 @@ AIR_PREC_BF16 = 2
 EXPORTED = ["air_default_options", "air_setup", "air_vcycle", "air_spmv", "air_gmres_solve",
             "air_hierarchy_levels", "air_hierarchy_info", "air_hierarchy_export", "air_free",
             "air_status_string", "air_kernel_launches", "air_gmres_solve_noalloc", "air_setup_timings",
-            "air_csr_transpose", "air_csr_outer"]
+            "air_csr_transpose", "air_csr_outer", "air_setup_batch", "air_gmres_solve_batch"]
 
 
 class air_csr(C.Structure):
@@ -101,6 +101,13 @@ def lib() -> C.CDLL:
     L.air_csr_transpose.restype = C.c_int
     L.air_csr_outer.argtypes = [C.POINTER(air_csr), C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p]
     L.air_csr_outer.restype = C.c_int
+    L.air_setup_batch.argtypes = [C.c_int, C.POINTER(air_csr), C.c_double, C.c_int, C.POINTER(air_options),
+                                  C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.POINTER(C.c_int)]
+    L.air_setup_batch.restype = C.c_int
+    L.air_gmres_solve_batch.argtypes = [C.c_int, C.POINTER(air_csr), C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                        C.POINTER(C.c_void_p), C.c_double, C.POINTER(C.c_void_p),
+                                        C.POINTER(air_solve_info), C.POINTER(C.c_int)]
+    L.air_gmres_solve_batch.restype = C.c_int
     _lib = L
     return L
 
@@ -377,3 +384,39 @@ class AdjointSolver:
 
     def solve(self, b, val=None):
         return _solve_fn().apply(b, self.A.val if val is None else val, self)
+
+
+# ------------------------------------------------------------------ batches
+def setup_batch(As, theta: float = 0.25, distance: int = 1, streams=None, **opts):
+    """air_setup_batch: independent setups at once (one host thread and stream each).
+
+    Returns (hierarchies, statuses); a failed problem has hierarchy None.
+    """
+    k = len(As)
+    o = default_options(**opts)
+    arr = (air_csr * k)(*[A.c() for A in As])
+    out = (C.c_void_p * k)()
+    st = (C.c_int * k)()
+    sp = None if streams is None else (C.c_void_p * k)(*[int(s.cuda_stream) for s in streams])
+    lib().air_setup_batch(k, arr, float(theta), int(distance), C.byref(o), sp, out, st)
+    hs = [Hierarchy(out[i], As[i], o.precision) if out[i] else None for i in range(k)]
+    return hs, [int(x) for x in st]
+
+
+def gmres_solve_batch(As, Hs, bs, xs=None, rtol: float = 1e-8, streams=None):
+    """air_gmres_solve_batch: independent device solves at once.  Returns (xs, infos, statuses)."""
+    import torch
+    k = len(As)
+    if xs is None:
+        xs = [torch.empty_like(b) for b in bs]
+    arr = (air_csr * k)(*[A.c() for A in As])
+    hp = (C.c_void_p * k)(*[H.handle.value for H in Hs])
+    bp = (C.c_void_p * k)(*[b.data_ptr() for b in bs])
+    xp = (C.c_void_p * k)(*[x.data_ptr() for x in xs])
+    inf = (air_solve_info * k)()
+    st = (C.c_int * k)()
+    sp = None if streams is None else (C.c_void_p * k)(*[int(s.cuda_stream) for s in streams])
+    r = lib().air_gmres_solve_batch(k, arr, hp, bp, xp, float(rtol), sp, inf, st)
+    if r < 0 and all(int(x) >= 0 for x in st):
+        _check(r, "air_gmres_solve_batch")
+    return xs, [inf[i] for i in range(k)], [int(x) for x in st]

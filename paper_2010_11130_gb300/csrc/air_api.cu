@@ -16,19 +16,35 @@ static std::atomic<unsigned long long> g_launches{0};
 unsigned long long air_launch_counter_add(unsigned long long k) { return g_launches.fetch_add(k) + k; }
 void air_launch_counter_sub(unsigned long long k) { g_launches.fetch_sub(k); }
 
+AirCallSlot &air_call_slot() {
+    thread_local AirCallSlot slot;
+    return slot;
+}
+
+cudaError_t air_dmalloc(void **p, size_t bytes) {
+    const AirCallSlot &c = air_call_slot();
+    return c.active ? cudaMallocAsync(p, bytes, c.s) : cudaMalloc(p, bytes);
+}
+
+void air_dfree(void *p) {
+    if (!p) return;
+    const AirCallSlot &c = air_call_slot();
+    if (c.active) cudaFreeAsync(p, c.s); else cudaFree(p);
+}
+
 namespace {
 
 template <typename T>
 int dalloc(T **p, int64_t count) {
     *p = nullptr;
     if (count <= 0) count = 1;
-    AIR_CUDA(cudaMalloc((void **)p, (size_t)count * sizeof(T)));
+    AIR_CUDA(air_dmalloc((void **)p, (size_t)count * sizeof(T)));
     return AIR_OK;
 }
 
 template <typename T>
 void dfree(T *&p) {
-    if (p) cudaFree((void *)p);
+    air_dfree((void *)p);
     p = nullptr;
 }
 
@@ -322,9 +338,9 @@ int setup_impl(const air_csr *A, const air_options *opt, cudaStream_t s, air_hie
             AIR_TRY(air_build_sell(L.nc, nullptr, L.rrp, L.rci, L.rv, opt->precision, 0, &L.sr, s));
         }
         size_t es = f32 ? sizeof(float) : sizeof(double);
-        AIR_CUDA(cudaMalloc(&L.b, (size_t)(L.n > 0 ? L.n : 1) * es));
-        AIR_CUDA(cudaMalloc(&L.x, (size_t)(L.n > 0 ? L.n : 1) * es));
-        AIR_CUDA(cudaMalloc(&L.x2, (size_t)(L.n > 0 ? L.n : 1) * es));
+        AIR_CUDA(air_dmalloc(&L.b, (size_t)(L.n > 0 ? L.n : 1) * es));
+        AIR_CUDA(air_dmalloc(&L.x, (size_t)(L.n > 0 ? L.n : 1) * es));
+        AIR_CUDA(air_dmalloc(&L.x2, (size_t)(L.n > 0 ? L.n : 1) * es));
     }
     {
         AirLevel &L0 = H->lev[0];
@@ -474,6 +490,7 @@ int air_setup(const air_csr *A, double theta, int distance, const air_options *o
     if (distance != 1) return AIR_ERR_UNSUPPORTED;
     air_hierarchy *H = new (std::nothrow) air_hierarchy();
     if (!H) return AIR_ERR_OOM;
+    AirCallStream call((cudaStream_t)stream);
     int st = setup_impl(A, &o, (cudaStream_t)stream, H);
     if (st != AIR_OK) {
         cudaStreamSynchronize((cudaStream_t)stream);
@@ -485,6 +502,7 @@ int air_setup(const air_csr *A, double theta, int distance, const air_options *o
 }
 
 int air_vcycle(const air_hierarchy *H, const double *b, double *x, void *stream) {
+    AirCallStream call((cudaStream_t)stream);
     if (!H || !b || !x) return AIR_ERR_INVALID_ARG;
     return air_vcycle_run(H, b, x, (cudaStream_t)stream);
 }
@@ -524,6 +542,7 @@ int air_csr_outer(const air_csr *A, const double *u, const double *w, double alp
 int air_gmres_solve(const air_csr *A, const air_hierarchy *H, const double *b, double *x, double rtol, void *stream,
                     air_solve_info *info) {
     if (!A || !H || !b || !x || !(rtol > 0.0) || A->n_rows != H->lev[0].n) return AIR_ERR_INVALID_ARG;
+    AirCallStream call((cudaStream_t)stream);
     air_solve_info local;
     if (!info) info = &local;
     cudaStream_t s = (cudaStream_t)stream;

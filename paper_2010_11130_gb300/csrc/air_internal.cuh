@@ -36,6 +36,33 @@ inline dim3 air_counted(dim3 g) {
     return g;
 }
 
+// Device memory of the library call in progress on this host thread.  While
+// an AirCallStream guard is alive, air_dmalloc / air_dfree are stream-ordered
+// (cudaMallocAsync / cudaFreeAsync on the call's stream) and never synchronise
+// the device, so calls on different streams from different host threads run
+// concurrently; outside a call they fall back to cudaMalloc / cudaFree.
+struct AirCallSlot {
+    cudaStream_t s = nullptr;
+    bool active = false;
+};
+AirCallSlot &air_call_slot();
+struct AirCallStream {
+    AirCallSlot prev;
+    explicit AirCallStream(cudaStream_t s) : prev(air_call_slot()) {
+        air_call_slot().s = s;
+        air_call_slot().active = true;
+    }
+    ~AirCallStream() { air_call_slot() = prev; }
+};
+cudaError_t air_dmalloc(void **p, size_t bytes);
+void air_dfree(void *p);
+
+// Every kernel with more than 48 KB of dynamic shared memory is opted in to
+// this one size (each launch checks its own need against it).  One value for
+// all calls: the attribute is per function, and setups running concurrently on
+// several host threads must not lower it under one another's launches.
+#define AIR_SMEM_OPTIN (200 * 1024)
+
 // device error flags written by bounded kernels
 #define AIR_DEVERR_RS_CAP 1
 #define AIR_DEVERR_CSR 2

@@ -567,10 +567,10 @@ int air_rs_first_pass_cursor(int64_t n, const int64_t *srp, const int32_t *sci, 
     const size_t smem = (size_t)NB_MAX * 16 * 4 + (size_t)nb * 2 * a.w2 * 4 + 3 * NB_MAX * 4 + (size_t)EMAX * 4 +
                         2 * (size_t)EMAX + 64;
     int st = AIR_OK;
-    if (smem > 200 * 1024) {
+    if (smem > AIR_SMEM_OPTIN) {
         st = AIR_ERR_UNSUPPORTED;
     } else {
-        AIR_CUDA(cudaFuncSetAttribute(rs5_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        AIR_CUDA(cudaFuncSetAttribute(rs5_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, AIR_SMEM_OPTIN));
         rs5_warp_kernel<<<air_counted(1), 32, smem, s>>>(a);
         AIR_LAUNCH();
         rs5_finish_kernel<<<air_counted(blocks_for(n, 256)), 256, 0, s>>>(n, lam, cf);

@@ -1356,8 +1356,8 @@ static int rs_first_pass_v4(int64_t n, const int64_t *srp, const int32_t *sci, c
     rs3_init_kernel<<<air_counted(grid_for(n, 256)), 256, 0, s>>>(i3);
     AIR_LAUNCH();
     size_t smem = (size_t)a.nb * a.w2 * sizeof(uint64_t) + (size_t)a.ent_cap * (sizeof(unsigned long long) + 2) + 16;
-    if (smem > 200 * 1024) return AIR_ERR_UNSUPPORTED;
-    AIR_CUDA(cudaFuncSetAttribute(rs4_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (smem > AIR_SMEM_OPTIN) return AIR_ERR_UNSUPPORTED;
+    AIR_CUDA(cudaFuncSetAttribute(rs4_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, AIR_SMEM_OPTIN));
     rs4_warp_kernel<<<air_counted(1), 32, smem, s>>>(a);
     AIR_LAUNCH();
     rs3_finish_kernel<<<air_counted(grid_for(n, 256)), 256, 0, s>>>(n, lam, cf);
@@ -1418,7 +1418,8 @@ static int rs_first_pass_v3(int64_t n, const int64_t *srp, const int32_t *sci, c
     rs3_init_kernel<<<air_counted(grid_for(n, 256)), 256, 0, s>>>(a);
     AIR_LAUNCH();
     size_t smem = (size_t)a.nb * a.w2 * sizeof(uint64_t) + (size_t)(max_st + 8);
-    AIR_CUDA(cudaFuncSetAttribute(rs3_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (smem > AIR_SMEM_OPTIN) return AIR_ERR_UNSUPPORTED;
+    AIR_CUDA(cudaFuncSetAttribute(rs3_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, AIR_SMEM_OPTIN));
     rs3_warp_kernel<<<air_counted(1), 32, smem, s>>>(a);
     AIR_LAUNCH();
     rs3_finish_kernel<<<air_counted(grid_for(n, 256)), 256, 0, s>>>(n, lam, cf);
@@ -1473,12 +1474,12 @@ int air_rs_first_pass(int64_t n, const int64_t *srp, const int32_t *sci, const i
     rs_init_kernel<<<air_counted(grid_for(n, 256)), 256, 0, s>>>(a);
     AIR_LAUNCH();
     size_t smem = (size_t)a.nb * a.w2 * sizeof(uint64_t) + (size_t)(max_st + 1 + a.touch_cap) * sizeof(int32_t);
-    if (smem > 200 * 1024) return AIR_ERR_UNSUPPORTED;
+    if (smem > AIR_SMEM_OPTIN) return AIR_ERR_UNSUPPORTED;
     if (cached) {
-        AIR_CUDA(cudaFuncSetAttribute(rs_warp_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        AIR_CUDA(cudaFuncSetAttribute(rs_warp_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, AIR_SMEM_OPTIN));
         rs_warp_kernel<true><<<air_counted(1), 32, smem, s>>>(a);
     } else {
-        AIR_CUDA(cudaFuncSetAttribute(rs_warp_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        AIR_CUDA(cudaFuncSetAttribute(rs_warp_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, AIR_SMEM_OPTIN));
         rs_warp_kernel<false><<<air_counted(1), 32, smem, s>>>(a);
     }
     AIR_LAUNCH();
@@ -1534,11 +1535,11 @@ int air_lair_solve(const AirLevel &L, int32_t max_m, int64_t *d_nsing, cudaStrea
     int warps = (int)((96 * 1024) / per_warp);
     if (warps > 8) warps = 8;
     if (warps < 1) {
-        if (per_warp > 200 * 1024) return AIR_ERR_UNSUPPORTED;
+        if (per_warp > AIR_SMEM_OPTIN) return AIR_ERR_UNSUPPORTED;
         warps = 1;
     }
     size_t smem = per_warp * warps;
-    AIR_CUDA(cudaFuncSetAttribute(lair_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    AIR_CUDA(cudaFuncSetAttribute(lair_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, AIR_SMEM_OPTIN));
     int64_t blocks = (L.nc + warps - 1) / warps;
     if (blocks > 152 * 16) blocks = 152 * 16;
     if (blocks < 1) blocks = 1;
@@ -1566,7 +1567,7 @@ int air_rap(const AirLevel &L, int64_t *acrp, int32_t *acci, double *acv, int32_
     int bits = 5;
     while ((1 << bits) < 2 * (max_terms > 1 ? max_terms : 1)) ++bits;
     size_t per_warp = (size_t)(1 << bits) * 20;
-    if (per_warp > 200 * 1024) return AIR_ERR_UNSUPPORTED;
+    if (per_warp > AIR_SMEM_OPTIN) return AIR_ERR_UNSUPPORTED;
     int warps = (int)((160 * 1024) / per_warp);
     if (warps > 8) warps = 8;
     if (warps < 1) warps = 1;
@@ -1575,11 +1576,11 @@ int air_rap(const AirLevel &L, int64_t *acrp, int32_t *acci, double *acv, int32_
     if (blocks > 152 * 16) blocks = 152 * 16;
     if (blocks < 1) blocks = 1;
     if (fill) {
-        AIR_CUDA(cudaFuncSetAttribute(rap_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        AIR_CUDA(cudaFuncSetAttribute(rap_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, AIR_SMEM_OPTIN));
         rap_kernel<true><<<air_counted((unsigned)blocks), warps * 32, smem, s>>>(L.nc, L.rrp, L.rci, L.rv, L.rp, L.ci, L.v, L.pcol,
                                                                    bits, nullptr, acrp, acci, acv);
     } else {
-        AIR_CUDA(cudaFuncSetAttribute(rap_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        AIR_CUDA(cudaFuncSetAttribute(rap_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, AIR_SMEM_OPTIN));
         rap_kernel<false><<<air_counted((unsigned)blocks), warps * 32, smem, s>>>(L.nc, L.rrp, L.rci, L.rv, L.rp, L.ci, L.v, L.pcol,
                                                                     bits, cnt, nullptr, nullptr, nullptr);
     }

@@ -644,7 +644,7 @@ int air_build_sell(int64_t m, const int32_t *rows_in, const int64_t *rp, const i
     air_free_sell(*out);
     out->m = m;
     const int64_t ns = (m + 31) / 32;
-    AIR_CUDA(cudaMalloc(&out->rows, (size_t)(m > 0 ? m : 1) * sizeof(int32_t)));
+    AIR_CUDA(air_dmalloc((void **)&out->rows, (size_t)(m > 0 ? m : 1) * sizeof(int32_t)));
     if (m > 0) {
         sell_sort_kernel<<<air_counted((unsigned)((m + SIGMA - 1) / SIGMA)), SIGMA / 2, 0, s>>>(m, rows_in, rp,
                                                                                               out->rows);
@@ -652,7 +652,7 @@ int air_build_sell(int64_t m, const int32_t *rows_in, const int64_t *rp, const i
     }
     const int32_t *rows = out->rows;
     int32_t *wid = nullptr;
-    AIR_CUDA(cudaMalloc(&out->ptr, (size_t)(ns + 1) * sizeof(int64_t)));
+    AIR_CUDA(air_dmalloc((void **)&out->ptr, (size_t)(ns + 1) * sizeof(int64_t)));
     AIR_CUDA(cudaMallocAsync(&wid, (size_t)(ns > 0 ? ns : 1) * sizeof(int32_t), s));
     sell_width_kernel<<<air_counted(grid_cap(ns, 256)), 256, 0, s>>>(m, rows, rp, wid);
     AIR_LAUNCH();
@@ -662,8 +662,8 @@ int air_build_sell(int64_t m, const int32_t *rows_in, const int64_t *rp, const i
     cudaFreeAsync(wid, s);
     const int64_t cnt = out->stored > 0 ? out->stored : 1;
     const size_t vb = precision == AIR_PREC_F64 ? 8 : (precision == AIR_PREC_F32 ? 4 : 2);
-    AIR_CUDA(cudaMalloc(&out->ci, (size_t)cnt * sizeof(int32_t)));
-    AIR_CUDA(cudaMalloc(&out->v, (size_t)cnt * vb));
+    AIR_CUDA(air_dmalloc((void **)&out->ci, (size_t)cnt * sizeof(int32_t)));
+    AIR_CUDA(air_dmalloc(&out->v, (size_t)cnt * vb));
     unsigned g = grid_cap(ns * 32, 256, 152 * 32);
     if (precision == AIR_PREC_F64)
         sell_fill_kernel<double, false><<<air_counted(g), 256, 0, s>>>(m, rows, rp, ci, v, out->ptr, out->ci,
@@ -682,10 +682,10 @@ int air_build_sell(int64_t m, const int32_t *rows_in, const int64_t *rp, const i
 }
 
 void air_free_sell(Sell &S) {
-    if (S.rows) cudaFree(S.rows);
-    if (S.ptr) cudaFree(S.ptr);
-    if (S.ci) cudaFree(S.ci);
-    if (S.v) cudaFree(S.v);
+    air_dfree(S.rows);
+    air_dfree(S.ptr);
+    air_dfree(S.ci);
+    air_dfree(S.v);
     S = Sell();
 }
 

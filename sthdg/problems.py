@@ -128,6 +128,27 @@ def rotating_pulse(n: int, p: int, nu: float, A: float = 0.1) -> Problem:
                    spec=("rotating_pulse", dict(n=n, p=p, nu=nu, A=A)))
 
 
+def batched_problems(count: int = 16, n_range=(16, 48), seed: int = 2010_11130):
+    """Independent 2D+time problems of uneven size for batched solves.
+
+    From numpy.random.default_rng(seed), per problem in order: n uniform on the
+    integers of n_range (inclusive), p uniform on {1, 2}, phi uniform on
+    [0, 2 pi), log10(nu) uniform on [-6, -2].  Velocity a = (cos phi, sin phi),
+    manufactured solution and source as manufactured_2d.  Returns the problems
+    and the generator (its next draws belong to the caller, e.g. extra
+    right-hand sides).
+    """
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        n = int(rng.integers(n_range[0], n_range[1] + 1))
+        p = int(rng.integers(1, 3))
+        phi = float(rng.uniform(0.0, 2.0 * PI))
+        nu = float(10.0 ** rng.uniform(-6.0, -2.0))
+        out.append(manufactured_2d(n=n, p=p, nu=nu, velocity="constant", a_const=(np.cos(phi), np.sin(phi))))
+    return out, rng
+
+
 def make(spec) -> Problem:
     """Rebuild a problem from its (factory name, kwargs) spec."""
     name, kw = spec

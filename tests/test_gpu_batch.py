@@ -1,0 +1,111 @@
+"""Independent problems at once: air_setup_batch / air_gmres_solve_batch.
+
+Each problem of a batch must come out exactly as from the single-problem
+calls (the same kernels run, only on concurrent streams), match the oracle,
+and report its own errors; concurrent setups must overlap on the GPU.
+"""
+import time
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+import paper_2010_11130_gb300 as air  # noqa: E402
+from sthdg import assemble  # noqa: E402
+from sthdg.problems import batched_problems, manufactured_2d  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    air.build()
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+
+
+_sys = {}
+
+
+def _systems():
+    if "b" not in _sys:
+        probs, _ = batched_problems(count=5, n_range=(3, 7))
+        _sys["b"] = [assemble(p) for p in probs]
+    return _sys["b"]
+
+
+def _levels_equal(H1, H2):
+    assert H1.levels() == H2.levels()
+    for l in range(H1.levels()):
+        for what in ("A.row_ptr", "A.col", "A.val"):
+            assert np.array_equal(H1.export(l, what), H2.export(l, what)), (l, what)
+        if H1.info(l).coarsest:
+            continue
+        for what in ("cf", "R.col", "R.val", "pcol"):
+            assert np.array_equal(H1.export(l, what), H2.export(l, what)), (l, what)
+
+
+def test_setup_batch_equals_single_setups_and_oracle():
+    ss = _systems()
+    As = [air.CSR.from_host(s.row_ptr, s.col, s.val) for s in ss]
+    Hs, st = air.setup_batch(As, theta=0.25, max_coarse=100)
+    assert st == [0] * len(ss)
+    for s, A, H in zip(ss, As, Hs):
+        _levels_equal(H, air.setup(A, theta=0.25, max_coarse=100))
+        O = oracle.setup(s.row_ptr, s.col, s.val, theta=0.25, max_coarse=100)
+        assert H.levels() == len(O.levels)
+        for l, OL in enumerate(O.levels):
+            if OL.nc:
+                assert np.array_equal(H.export(l, "cf"), OL.cf)
+                assert np.array_equal(H.export(l, "R.val"), OL.R[2])
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_solve_batch_equals_single_solves(precision):
+    ss = _systems()
+    As = [air.CSR.from_host(s.row_ptr, s.col, s.val) for s in ss]
+    Hs, _ = air.setup_batch(As, theta=0.25, max_coarse=100, precision=precision)
+    bs = [torch.from_numpy(np.ascontiguousarray(s.rhs)).cuda() for s in ss]
+    xs, infos, st = air.gmres_solve_batch(As, Hs, bs, rtol=1e-8)
+    assert st == [0] * len(ss)
+    for A, H, b, x, inf in zip(As, Hs, bs, xs, infos):
+        x1, inf1 = air.gmres_solve(A, H, b, rtol=1e-8)
+        torch.cuda.synchronize()
+        assert inf.iters == inf1.iters and inf.relres == inf1.relres
+        assert torch.equal(x, x1)
+
+
+def test_batch_reports_each_problem_status():
+    ss = _systems()[:3]
+    As = [air.CSR.from_host(s.row_ptr, s.col, s.val) for s in ss]
+    bad = ss[1]
+    col = bad.col.copy()
+    col[5] = bad.n + 7                                      # out-of-range column in problem 1 only
+    As[1] = air.CSR.from_host(bad.row_ptr, col, bad.val)
+    Hs, st = air.setup_batch(As, theta=0.25, max_coarse=100)
+    assert st[0] == 0 and st[2] == 0 and st[1] == -2
+    assert Hs[1] is None and Hs[0] is not None and Hs[2] is not None
+    b = [torch.from_numpy(np.ascontiguousarray(ss[0].rhs)).cuda()] * 2
+    with pytest.raises(air.AirError) as e:                 # one hierarchy twice in a solve batch
+        air.gmres_solve_batch([As[0], As[0]], [Hs[0], Hs[0]], b)
+    assert e.value.status == -1
+
+
+def test_concurrent_setups_overlap():
+    # four identical mid-size systems: the first pass of each runs on one SM, so
+    # the batch takes much less than four single setups
+    s = assemble(manufactured_2d(10, 2, 1e-6))
+    As = [air.CSR.from_host(s.row_ptr, s.col, s.val) for _ in range(4)]
+    air.setup(As[0])                                         # warm-up (module load, pools)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for A in As:
+        air.setup(A)
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    Hs, st = air.setup_batch(As)
+    torch.cuda.synchronize()
+    t_bat = time.perf_counter() - t0
+    assert st == [0] * 4
+    assert t_bat < 0.7 * t_seq, (t_bat, t_seq)

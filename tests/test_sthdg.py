@@ -176,3 +176,16 @@ def test_rotating_pulse_error_magnitude_table1(p, nu, paper):
     s = assemble(pr, keep_local=True)
     err = l2_error(s, pr, _solve(s))
     assert paper / 4.0 < err < paper * 4.0
+
+
+def test_batched_problem_recipe():
+    """Seeded recipe of the independent-problem batch: n on the integer range,
+    p in {1, 2}, nu in [1e-6, 1e-2], unit velocity; reproducible."""
+    from sthdg.problems import batched_problems
+    ps, _ = batched_problems(count=16, n_range=(16, 48))
+    qs, _ = batched_problems(count=16, n_range=(16, 48))
+    assert [(p.n, p.p, p.nu) for p in ps] == [(q.n, q.p, q.nu) for q in qs]
+    for p in ps:
+        assert 16 <= p.n <= 48 and p.p in (1, 2) and 1e-6 <= p.nu <= 1e-2
+        a = p.velocity(np.zeros((1, 3)))[0]
+        assert abs(np.hypot(*a) - 1.0) < 1e-14
