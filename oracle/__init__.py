@@ -54,6 +54,9 @@ def _load():
     lib.ora_gmres.argtypes = [C.c_int64, I64P, I32P, F64P, C.c_void_p, F64P, F64P, C.c_double,
                               C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double), C.c_void_p]
     lib.ora_gmres.restype = C.c_int
+    lib.ora_bicgstab.argtypes = [C.c_int64, I64P, I32P, F64P, C.c_void_p, F64P, F64P, C.c_double, C.c_int,
+                                 C.POINTER(C.c_int), C.POINTER(C.c_double)]
+    lib.ora_bicgstab.restype = C.c_int
     _lib = lib
     return lib
 
@@ -163,3 +166,19 @@ def gmres(row_ptr, col, val, H, b, rtol=1e-8, restart=30, max_iter=1000):
                        int(restart), int(max_iter), C.byref(it), C.byref(rr),
                        hist.ctypes.data_as(C.c_void_p))
     return x, it.value, rr.value, rc == 0, hist[: it.value + 1]
+
+
+def bicgstab(row_ptr, col, val, H, b, rtol=1e-12, max_iter=1000):
+    """Right-preconditioned BiCGSTAB with one V-cycle of H as M^{-1} (identity if H is None).
+
+    Returns (x, iterations, true relative residual, converged)."""
+    lib = _load()
+    rp, ci, v = _csr(row_ptr, col, val)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.zeros_like(b)
+    it = C.c_int(0)
+    rr = C.c_double(0.0)
+    rc = lib.ora_bicgstab(len(rp) - 1, rp, ci, v, H._h if H is not None else None, b, x, float(rtol),
+                          int(max_iter), C.byref(it), C.byref(rr))
+    return x, it.value, rr.value, rc == 0
+

@@ -677,6 +677,78 @@ done:
     return conv ? 0 : 1;
 }
 
+/* ------------------------------------------------------------ BiCGSTAB */
+/* Right-preconditioned BiCGSTAB (van der Vorst, 1992), the Krylov method the
+ * paper pairs with AIR (Section 5.1, Table 2): M^{-1} = one V-cycle (identity
+ * when H is NULL), x0 = 0, shadow residual r^ = r0.  Per iteration:
+ *   rho = (r^, r); beta = (rho / rho_prev)(alpha / omega);
+ *   p = r + beta (p - omega v); p^ = M^{-1} p; v = A p^; alpha = rho / (r^, v);
+ *   s = r - alpha v; s^ = M^{-1} s; t = A s^; omega = (t, s) / (t, t);
+ *   x += alpha p^ + omega s^; r = s - omega t.
+ * Stop when ||r|| / ||b|| <= rtol and the true residual b - A x agrees; if the
+ * true residual is still above rtol the iteration restarts from it (r^ = r,
+ * p = v = 0, rho_prev = alpha = omega = 1).  rho = 0, (r^, v) = 0 or omega = 0
+ * end the solve unconverged.  iters counts iterations (two V-cycles each);
+ * relres is the true relative residual at exit.  Returns 0 if converged. */
+int ora_bicgstab(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
+                 const ora_hier *H, const double *b, double *x, double rtol, int max_iter,
+                 int *iters, double *relres) {
+    double *r = (double *)malloc((size_t)n * sizeof(double));
+    double *rh = (double *)malloc((size_t)n * sizeof(double));
+    double *p = (double *)calloc((size_t)n, sizeof(double));
+    double *vv = (double *)calloc((size_t)n, sizeof(double));
+    double *ph = (double *)malloc((size_t)n * sizeof(double));
+    double *s = (double *)malloc((size_t)n * sizeof(double));
+    double *sh = (double *)malloc((size_t)n * sizeof(double));
+    double *t = (double *)malloc((size_t)n * sizeof(double));
+    int it = 0, conv = 0;
+    double bn = sqrt(dot(n, b, b));
+    for (int64_t i = 0; i < n; ++i) { x[i] = 0.0; r[i] = b[i]; rh[i] = b[i]; }
+    *relres = 0.0;
+    if (bn == 0.0) { conv = 1; goto done; }
+    *relres = 1.0;
+    double rho_prev = 1.0, alpha = 1.0, omega = 1.0;
+    while (it < max_iter) {
+        double rho = dot(n, rh, r);
+        if (rho == 0.0) break;
+        double beta = (rho / rho_prev) * (alpha / omega);
+        for (int64_t i = 0; i < n; ++i) p[i] = r[i] + beta * (p[i] - omega * vv[i]);
+        if (H) ora_vcycle(H, p, ph); else memcpy(ph, p, (size_t)n * sizeof(double));
+        ora_spmv(n, rp, ci, v, ph, vv);
+        double den = dot(n, rh, vv);
+        if (den == 0.0) break;
+        alpha = rho / den;
+        for (int64_t i = 0; i < n; ++i) s[i] = r[i] - alpha * vv[i];
+        if (H) ora_vcycle(H, s, sh); else memcpy(sh, s, (size_t)n * sizeof(double));
+        ora_spmv(n, rp, ci, v, sh, t);
+        double tt = dot(n, t, t), ts = dot(n, t, s);
+        omega = tt > 0.0 ? ts / tt : 0.0;
+        for (int64_t i = 0; i < n; ++i) x[i] += alpha * ph[i] + omega * sh[i];
+        for (int64_t i = 0; i < n; ++i) r[i] = s[i] - omega * t[i];
+        rho_prev = rho;
+        ++it;
+        if (sqrt(dot(n, r, r)) / bn <= rtol) {
+            ora_spmv(n, rp, ci, v, x, t);                       /* true residual */
+            for (int64_t i = 0; i < n; ++i) r[i] = b[i] - t[i];
+            *relres = sqrt(dot(n, r, r)) / bn;
+            if (*relres <= rtol) { conv = 1; break; }
+            for (int64_t i = 0; i < n; ++i) { rh[i] = r[i]; p[i] = 0.0; vv[i] = 0.0; }
+            rho_prev = alpha = omega = 1.0;
+            continue;
+        }
+        if (omega == 0.0) break;
+    }
+    if (!conv) {
+        ora_spmv(n, rp, ci, v, x, t);
+        for (int64_t i = 0; i < n; ++i) r[i] = b[i] - t[i];
+        *relres = sqrt(dot(n, r, r)) / bn;
+    }
+done:
+    *iters = it;
+    free(r); free(rh); free(p); free(vv); free(ph); free(s); free(sh); free(t);
+    return conv ? 0 : 1;
+}
+
 /* ------------------------------------------------------------ accessors */
 int ora_nlevels(const ora_hier *H) { return H ? H->nlev : 0; }
 

@@ -289,3 +289,41 @@ def test_coarsening_stops_and_levels_shrink():
     ns = [L.n for L in H.levels]
     assert ns[-1] <= 200
     assert all(b < 0.9 * a for a, b in zip(ns[:-1], ns[1:]))
+
+
+# ------------------------------------------------------------------ BiCGSTAB
+def test_bicgstab_unpreconditioned_matches_dense_solve():
+    """Without a preconditioner BiCGSTAB is the plain van der Vorst iteration:
+    on a small nonsymmetric trace system it reaches the dense solution."""
+    s = assemble(manufactured_2d(2, 1, 1e-2))
+    x, it, rr, ok = oracle.bicgstab(s.row_ptr, s.col, s.val, None, s.rhs, rtol=1e-12, max_iter=2000)
+    A = _sp(s.row_ptr, s.col, s.val, (s.n, s.n)).toarray()
+    xd = np.linalg.solve(A, s.rhs)
+    assert ok and rr <= 1e-12 and it > 1
+    assert np.linalg.norm(x - xd) <= 1e-9 * np.linalg.norm(xd)
+
+
+def test_bicgstab_with_exact_preconditioner_takes_one_iteration():
+    """With M^{-1} = A^{-1} (the exact two-level reduction of pure advection,
+    as in the test above) the first iteration gives p^ = A^{-1} b, alpha = 1,
+    s = 0: BiCGSTAB stops after one iteration."""
+    s = assemble(pure_advection(3, 2, 1))
+    H = oracle.setup(s.row_ptr, s.col, s.val, theta=1e-12, distance=s.n, max_coarse=0,
+                     max_levels=2, max_dense=s.n, relax="F" * 40)
+    x, it, rr, ok = oracle.bicgstab(s.row_ptr, s.col, s.val, H, s.rhs, rtol=1e-10)
+    assert ok and it == 1 and rr <= 1e-10
+
+
+def test_bicgstab_with_air_matches_scipy_solution(sys2d):
+    """AIR-preconditioned BiCGSTAB solves the system to 1e-12 (Section 5.1 uses
+    this tolerance); the solution agrees with scipy's unpreconditioned BiCGSTAB
+    run to the same tolerance."""
+    import scipy.sparse.linalg as spl
+    s = sys2d
+    H = oracle.setup(s.row_ptr, s.col, s.val, theta=0.25, max_coarse=100)
+    x, it, rr, ok = oracle.bicgstab(s.row_ptr, s.col, s.val, H, s.rhs, rtol=1e-12)
+    assert ok and rr <= 1e-12
+    A = _sp(s.row_ptr, s.col, s.val, (s.n, s.n))
+    xs, info = spl.bicgstab(A, s.rhs, rtol=1e-13, maxiter=20000)
+    assert info == 0
+    assert np.linalg.norm(x - xs) <= 1e-8 * np.linalg.norm(xs)
