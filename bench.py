@@ -323,6 +323,17 @@ def run_ours(args):
         _, inf_s = air.gmres_solve(A, H, b, xs, rtol=args.rtol)
         torch.cuda.synchronize()
         t_solve = time.perf_counter() - t0
+        if key == "f64":
+            # the paper's Krylov method on the same hierarchy: BiCGSTAB to the metric's
+            # tolerance and to the paper's 1e-12
+            bic = {}
+            for tol in (args.rtol, 1e-12):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                _, inf_b = air.bicgstab_solve(A, H, b, torch.empty_like(b), rtol=tol)
+                torch.cuda.synchronize()
+                bic[f"{tol:g}"] = {"s": time.perf_counter() - t0, "iters": inf_b.iters,
+                                   "relres": inf_b.relres, "status": inf_b.status}
         breakdown[key] = {"setup_s": t_setup, "solve_s": t_solve, "iters": inf_s.iters,
                           "setup_phase_ms": H.setup_timings(), "levels": H.levels()}
         vb = vcycle_bytes(H, {1: 4, 0: 8, 2: 2}[prec], diag_bytes=4 if prec == 2 else 0)
@@ -396,6 +407,7 @@ def run_ours(args):
                           "achieved": sb / t_spmv / 1e9, "peak": gbs_peak, "unit": "GB/s",
                           "frac": sb / t_spmv / 1e9 / gbs_peak, "algorithmic_bytes": sb, "launch_s": t_spmv},
         "breakdown": breakdown,
+        "bicgstab_f64_hierarchy": bic,
         "dominant_kernel": {
             "kernel": "rs5_warp_kernel (sequential first-pass C/F splitting, one warp per level)",
             "bound": "latency (one dependent chain of picks; no HBM or ALU roofline applies)",

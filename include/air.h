@@ -121,6 +121,19 @@ int air_vcycle(const air_hierarchy *H, const double *b, double *x, void *stream)
 /* y = A x for device CSR A and device vectors.  Asynchronous. */
 int air_spmv(const air_csr *A, const double *x, double *y, void *stream);
 
+/* BiCGSTAB preconditioned on the right by one V-cycle of H (van der Vorst,
+ * 1992): the Krylov method of the paper's experiments (Section 5.1, Table 2,
+ * stopping at relative residual 1e-12).  x0 = 0, shadow residual r0 = b.  It
+ * stops when the recursive residual and then the true residual ||b - A x|| /
+ * ||b|| are <= rtol; a true residual above rtol restarts the iteration from
+ * it.  A breakdown ((r^, r) = 0, (r^, v) = 0) or omega = 0 ends it.  Same
+ * arguments, buffers, ownership and status as air_gmres_solve; info->iters
+ * counts BiCGSTAB iterations (two V-cycles each), info->restarts the
+ * restarts from the true residual.  Synchronises the stream four times per
+ * iteration (the scalar recurrence runs on the host). */
+int air_bicgstab_solve(const air_csr *A, const air_hierarchy *H, const double *b, double *x, double rtol,
+                       void *stream, air_solve_info *info);
+
 /* Independent problems at once.  The paper solves one system at a time;
  * these run count independent setups (or solves) concurrently, one host
  * thread and one stream per problem (streams[k], or a library-created stream

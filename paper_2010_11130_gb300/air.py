@@ -24,7 +24,8 @@ AIR_PREC_BF16 = 2
 EXPORTED = ["air_default_options", "air_setup", "air_vcycle", "air_spmv", "air_gmres_solve",
             "air_hierarchy_levels", "air_hierarchy_info", "air_hierarchy_export", "air_free",
             "air_status_string", "air_kernel_launches", "air_gmres_solve_noalloc", "air_setup_timings",
-            "air_csr_transpose", "air_csr_outer", "air_setup_batch", "air_gmres_solve_batch"]
+            "air_csr_transpose", "air_csr_outer", "air_setup_batch", "air_gmres_solve_batch",
+            "air_bicgstab_solve"]
 
 
 class air_csr(C.Structure):
@@ -101,6 +102,9 @@ def lib() -> C.CDLL:
     L.air_csr_transpose.restype = C.c_int
     L.air_csr_outer.argtypes = [C.POINTER(air_csr), C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p]
     L.air_csr_outer.restype = C.c_int
+    L.air_bicgstab_solve.argtypes = [C.POINTER(air_csr), C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
+                                     C.c_void_p, C.POINTER(air_solve_info)]
+    L.air_bicgstab_solve.restype = C.c_int
     L.air_setup_batch.argtypes = [C.c_int, C.POINTER(air_csr), C.c_double, C.c_int, C.POINTER(air_options),
                                   C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.POINTER(C.c_int)]
     L.air_setup_batch.restype = C.c_int
@@ -274,6 +278,25 @@ def gmres_solve(A: CSR, H: Hierarchy, b, x=None, rtol: float = 1e-8, stream=None
     st = lib().air_gmres_solve(C.byref(Ac), H.handle, C.c_void_p(bp), C.c_void_p(xp), float(rtol),
                                C.c_void_p(sp), C.byref(inf))
     _check(st, "air_gmres_solve")
+    return x, inf
+
+
+def bicgstab_solve(A: CSR, H: Hierarchy, b, x=None, rtol: float = 1e-12, stream=None):
+    """air_bicgstab_solve.  Device tensors for device A; numpy arrays for host A."""
+    Ac = A.c()
+    inf = air_solve_info()
+    if Ac.on_device:
+        import torch
+        if x is None:
+            x = torch.empty_like(b)
+        bp, xp, sp = b.data_ptr(), x.data_ptr(), _stream(stream)
+    else:
+        if x is None:
+            x = np.empty_like(b)
+        bp, xp, sp = b.ctypes.data, x.ctypes.data, 0
+    st = lib().air_bicgstab_solve(C.byref(Ac), H.handle, C.c_void_p(bp), C.c_void_p(xp), float(rtol),
+                                  C.c_void_p(sp), C.byref(inf))
+    _check(st, "air_bicgstab_solve")
     return x, inf
 
 

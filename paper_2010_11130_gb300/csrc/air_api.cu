@@ -449,6 +449,97 @@ int gmres_impl(const AirLevel &A0, const air_hierarchy *Hc, const double *b, dou
     return info->status;
 }
 
+// Right-preconditioned BiCGSTAB (van der Vorst, 1992), the Krylov method the
+// paper pairs with AIR (Section 5.1): the same iteration, restarts and stopping
+// test as the oracle's, with dot products reduced on the device and the scalar
+// recurrence (rho, alpha, omega) on the host, four small reads per iteration.
+int bicgstab_impl(const AirLevel &A0, const air_hierarchy *Hc, const double *b, double *x, double rtol,
+                  cudaStream_t s, air_solve_info *info) {
+    air_hierarchy *H = const_cast<air_hierarchy *>(Hc);
+    const int64_t n = A0.n;
+    AIR_TRY(ensure_workspace(H, n, H->opt.restart > 8 ? H->opt.restart : 8));
+    const int nblk = air_reduce_nblk(n);
+    double *r = H->V, *rh = H->V + n, *p = H->V + 2 * n, *v = H->V + 3 * n;
+    double *sv = H->V + 4 * n, *t = H->V + 5 * n, *ph = H->V + 6 * n, *sh = H->V + 7 * n;   // s, t adjacent
+    double *sc = H->scal;
+    auto fetch = [&](int k) -> int {
+        AIR_CUDA(cudaMemcpyAsync(H->h_est, sc, (size_t)k * sizeof(double), cudaMemcpyDeviceToHost, s));
+        AIR_CUDA(cudaStreamSynchronize(s));
+        return AIR_OK;
+    };
+    auto dots = [&](const double *V, int k, const double *w) -> int {   // sc[i] = V_i . w, i < k
+        AIR_TRY(air_dot_partials(n, V, n, k, w, H->partials, nblk, s));
+        AIR_TRY(air_reduce_partials(k, H->partials, nblk, sc, s));
+        return fetch(k);
+    };
+    info->iters = 0;
+    info->restarts = 0;
+    info->vcycles = 0;
+    info->relres = 0.0;
+    info->status = AIR_NOT_CONVERGED;
+    AIR_TRY(air_fill_zero(x, n, s));
+    AIR_TRY(dots(b, 1, b));
+    const double bn = sqrt(H->h_est[0]);
+    if (bn == 0.0) {
+        info->status = AIR_OK;
+        return AIR_OK;
+    }
+    AIR_CUDA(cudaMemcpyAsync(r, b, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    AIR_CUDA(cudaMemcpyAsync(rh, b, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    AIR_TRY(air_fill_zero(p, n, s));
+    AIR_TRY(air_fill_zero(v, n, s));
+    double rho_prev = 1.0, alpha = 1.0, omega = 1.0;
+    info->relres = 1.0;
+    bool conv = false;
+    int it = 0;
+    while (it < H->opt.max_iter) {
+        AIR_TRY(dots(rh, 1, r));
+        const double rho = H->h_est[0];
+        if (rho == 0.0) break;
+        const double beta = (rho / rho_prev) * (alpha / omega);
+        AIR_TRY(air_lincomb(n, p, r, 1.0, p, beta, v, -beta * omega, s));        // p = r + beta (p - omega v)
+        AIR_TRY(air_vcycle_run(H, p, ph, s));
+        AIR_TRY(air_sell_spmv_f64(H->a0, ph, v, nullptr, s));
+        AIR_TRY(dots(rh, 1, v));
+        const double den = H->h_est[0];
+        if (den == 0.0) break;
+        alpha = rho / den;
+        AIR_TRY(air_lincomb(n, sv, r, 1.0, v, -alpha, nullptr, 0.0, s));          // s = r - alpha v
+        AIR_TRY(air_vcycle_run(H, sv, sh, s));
+        AIR_TRY(air_sell_spmv_f64(H->a0, sh, t, nullptr, s));
+        AIR_TRY(dots(sv, 2, t));                                                  // (s, t), (t, t)
+        const double ts = H->h_est[0], tt = H->h_est[1];
+        omega = tt > 0.0 ? ts / tt : 0.0;
+        AIR_TRY(air_lincomb(n, x, x, 1.0, ph, alpha, sh, omega, s));              // x += alpha p^ + omega s^
+        AIR_TRY(air_lincomb(n, r, sv, 1.0, t, -omega, nullptr, 0.0, s));          // r = s - omega t
+        info->vcycles += 2;
+        rho_prev = rho;
+        ++it;
+        AIR_TRY(dots(r, 1, r));
+        if (sqrt(H->h_est[0]) / bn <= rtol) {
+            AIR_TRY(air_sell_spmv_f64(H->a0, x, r, b, s));                       // true residual b - A x
+            AIR_TRY(dots(r, 1, r));
+            info->relres = sqrt(H->h_est[0]) / bn;
+            if (info->relres <= rtol) { conv = true; break; }
+            AIR_CUDA(cudaMemcpyAsync(rh, r, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            AIR_TRY(air_fill_zero(p, n, s));
+            AIR_TRY(air_fill_zero(v, n, s));
+            rho_prev = alpha = omega = 1.0;
+            info->restarts++;
+            continue;
+        }
+        if (omega == 0.0) break;
+    }
+    if (!conv) {
+        AIR_TRY(air_sell_spmv_f64(H->a0, x, r, b, s));
+        AIR_TRY(dots(r, 1, r));
+        info->relres = sqrt(H->h_est[0]) / bn;
+    }
+    info->iters = it;
+    info->status = conv ? AIR_OK : AIR_NOT_CONVERGED;
+    return info->status;
+}
+
 }  // namespace
 
 extern "C" {
@@ -510,6 +601,27 @@ int air_vcycle(const air_hierarchy *H, const double *b, double *x, void *stream)
 int air_spmv(const air_csr *A, const double *x, double *y, void *stream) {
     if (!A || !x || !y || !A->on_device || A->n_rows <= 0) return AIR_ERR_INVALID_ARG;
     return air_spmv_f64(A->n_rows, A->row_ptr, A->col, A->val, x, y, nullptr, (cudaStream_t)stream, A->nnz, 0);
+}
+
+int air_bicgstab_solve(const air_csr *A, const air_hierarchy *H, const double *b, double *x, double rtol,
+                       void *stream, air_solve_info *info) {
+    if (!A || !H || !b || !x || !(rtol > 0.0) || A->n_rows != H->lev[0].n) return AIR_ERR_INVALID_ARG;
+    AirCallStream call((cudaStream_t)stream);
+    air_solve_info local;
+    if (!info) info = &local;
+    cudaStream_t s = (cudaStream_t)stream;
+    air_hierarchy *Hm = const_cast<air_hierarchy *>(H);
+    const int64_t n = A->n_rows;
+    if (A->on_device) return bicgstab_impl(H->lev[0], H, b, x, rtol, s, info);
+    if (!H->lev[0].owns_A || H->lev[0].v == nullptr) return AIR_ERR_INVALID_ARG;
+    if (!Hm->bd) AIR_TRY(dalloc(&Hm->bd, n));
+    if (!Hm->xd) AIR_TRY(dalloc(&Hm->xd, n));
+    AIR_CUDA(cudaMemcpyAsync(Hm->bd, b, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, s));
+    const int st = bicgstab_impl(H->lev[0], H, Hm->bd, Hm->xd, rtol, s, info);
+    if (st < 0) return st;
+    AIR_CUDA(cudaMemcpyAsync(x, Hm->xd, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    AIR_CUDA(cudaStreamSynchronize(s));
+    return st;
 }
 
 int air_csr_transpose(const air_csr *A, int64_t *row_ptr_t, int32_t *col_t, double *val_t, void *stream) {

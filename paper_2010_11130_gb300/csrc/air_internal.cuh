@@ -200,6 +200,8 @@ int air_max_row(int64_t n, const int64_t *rp, int32_t *out_max, cudaStream_t s);
 int air_vcycle_run(const air_hierarchy *H, const double *b, double *x, cudaStream_t s, int use_graph = 1);
 int air_point_list(int64_t n, const int8_t *cf, int which, int32_t *list, int64_t *work, cudaStream_t s);
 int air_cast_d2f(const double *in, float *out, int64_t n, cudaStream_t s);
+int air_lincomb(int64_t n, double *out, const double *a, double ca, const double *b, double cb, const double *c,
+                double cc, cudaStream_t s);
 int air_cast_bf16(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, void *out16, float *diag32,
                   cudaStream_t s);
 int air_build_sell(int64_t m, const int32_t *rows, const int64_t *rp, const int32_t *ci, const double *v,

@@ -467,6 +467,16 @@ __global__ void axpy_multi_kernel(int64_t n, const double *__restrict__ Z, int64
 
 __global__ void set_scalar_kernel(double *p, double v) { *p = v; }
 
+// out = ca a + cb b (+ cc c when c != NULL); out may alias any input (elementwise)
+__global__ void lincomb_kernel(int64_t n, double *out, const double *a, double ca, const double *b, double cb,
+                               const double *c, double cc) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double v = ca * a[i] + cb * b[i];
+        if (c) v += cc * c[i];
+        out[i] = v;
+    }
+}
+
 template <int U, typename TV, typename TX, int MODE>
 void launch_row(const RowArgs<TV, TX> &a, cudaStream_t s) {
     unsigned g = grid_cap(a.n * 4, 256, 152 * 16);
@@ -780,6 +790,14 @@ int air_axpy_multi(int64_t n, const double *Z, int64_t ldz, int k, const double 
 
 int air_fill_zero(double *x, int64_t n, cudaStream_t s) {
     AIR_CUDA(cudaMemsetAsync(x, 0, (size_t)n * sizeof(double), s));
+    return AIR_OK;
+}
+
+int air_lincomb(int64_t n, double *out, const double *a, double ca, const double *b, double cb, const double *c,
+                double cc, cudaStream_t s) {
+    if (n <= 0) return AIR_OK;
+    lincomb_kernel<<<air_counted(grid_cap(n, 256)), 256, 0, s>>>(n, out, a, ca, b, cb, c, cc);
+    AIR_LAUNCH();
     return AIR_OK;
 }
 
