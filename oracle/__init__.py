@@ -41,7 +41,7 @@ def _load():
     lib = C.CDLL(build())
     lib.ora_spmv.argtypes = [C.c_int64, I64P, I32P, F64P, F64P, F64P]
     lib.ora_spmv.restype = None
-    lib.ora_setup.argtypes = [C.c_int64, I64P, I32P, F64P, C.c_double, C.c_int, C.c_int, C.c_int,
+    lib.ora_setup.argtypes = [C.c_int64, I64P, I32P, F64P, C.c_double, C.c_double, C.c_int, C.c_int, C.c_int,
                               C.c_int, C.c_char_p, C.c_double, C.POINTER(C.c_int)]
     lib.ora_setup.restype = C.c_void_p
     lib.ora_free.argtypes = [C.c_void_p]
@@ -136,12 +136,16 @@ class OracleError(RuntimeError):
 
 
 def setup(row_ptr, col, val, theta=0.25, distance=1, max_coarse=1000, max_levels=25,
-          max_dense=4096, relax="FCF", omega=1.0) -> Hierarchy:
-    """Build the AIR hierarchy (strength, RS splitting, l-AIR R, one-point P, RAP)."""
+          max_dense=4096, relax="FCF", omega=1.0, theta_r=None) -> Hierarchy:
+    """Build the AIR hierarchy (strength, RS splitting, l-AIR R, one-point P, RAP).
+
+    theta is the strength threshold of the C/F splitting and one-point P;
+    theta_r (default: theta) that of the l-AIR neighbourhoods of R."""
     lib = _load()
     rp, ci, v = _csr(row_ptr, col, val)
     st = C.c_int(0)
-    h = lib.ora_setup(len(rp) - 1, rp, ci, v, float(theta), int(distance), int(max_coarse),
+    h = lib.ora_setup(len(rp) - 1, rp, ci, v, float(theta), float(theta if theta_r is None else theta_r),
+                      int(distance), int(max_coarse),
                       int(max_levels), int(max_dense), relax.encode(), float(omega), C.byref(st))
     if not h:
         raise OracleError(f"oracle setup failed with status {st.value}")

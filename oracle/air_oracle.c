@@ -22,6 +22,9 @@
  *    undecided k in S_j of a new F point j gains 1; every undecided k in
  *    S_i loses 1.  Points with S_i and S^T_i both empty start as F; points
  *    still undecided when the largest lambda is 0 become F.
+ *  - the strength threshold may differ between the C/F splitting (with
+ *    one-point P) and the l-AIR neighbourhoods (Section 4 uses 0.2 for the
+ *    coarsening and 0.3 for R); R then uses its own strength graph.
  *  - l-AIR neighbourhood N_i: distance 1 = S_i intersect F; distance d adds
  *    S_k intersect F for every k found at distance d-1.  N_i ascending.
  *    Local system A_ff(N_i,N_i)^T z = -A(i,N_i)^T by LU with partial
@@ -68,6 +71,7 @@ typedef struct {
     ora_csr A;          /* level operator */
     ora_csr S;          /* strength pattern (v unused) */
     ora_csr ST;         /* its transpose */
+    ora_csr SR;         /* strength pattern for R when its threshold differs (else empty) */
     int8_t *cf;         /* 1 = C, 0 = F */
     int32_t *cid;       /* coarse id of C points, -1 for F */
     int64_t nc;
@@ -338,7 +342,7 @@ static int64_t lair_neighbourhood(const ora_csr *S, const int8_t *cf, int64_t i,
 }
 
 static int build_R(ora_level *L, int distance) {
-    const ora_csr *A = &L->A, *S = &L->S;
+    const ora_csr *A = &L->A, *S = L->SR.rp ? &L->SR : &L->S;
     int64_t n = A->n;
     int32_t *mark = (int32_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
     int32_t *nb = (int32_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
@@ -476,7 +480,7 @@ static int galerkin(const ora_level *L, ora_csr *Ac) {
 void ora_free(ora_hier *H);
 
 ora_hier *ora_setup(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
-                    double theta, int distance, int max_coarse, int max_levels,
+                    double theta, double theta_r, int distance, int max_coarse, int max_levels,
                     int max_dense, const char *relax, double omega, int *status) {
     *status = ORA_OK;
     if (n <= 0 || max_levels < 1 || max_levels > ORA_MAX_LEVELS || distance < 1) { *status = ORA_ERR_ARG; return NULL; }
@@ -511,6 +515,7 @@ ora_hier *ora_setup(int64_t n, const int64_t *rp, const int32_t *ci, const doubl
             free(L->cf); free(L->cid); L->cf = NULL; L->cid = NULL; L->nc = 0;
             break;
         }
+        if (theta_r >= 0.0 && theta_r != theta && (*status = strength(&L->A, theta_r, &L->SR))) return H;
         if ((*status = build_R(L, distance))) return H;
         L->pcol = (int32_t *)malloc((size_t)nl * sizeof(int32_t));
         L->pw = (double *)malloc((size_t)nl * sizeof(double));
@@ -540,7 +545,7 @@ void ora_free(ora_hier *H) {
     if (!H) return;
     for (int l = 0; l < ORA_MAX_LEVELS; ++l) {
         ora_level *L = &H->lev[l];
-        csr_free(&L->A); csr_free(&L->S); csr_free(&L->ST); csr_free(&L->R);
+        csr_free(&L->A); csr_free(&L->S); csr_free(&L->ST); csr_free(&L->SR); csr_free(&L->R);
         free(L->cf); free(L->cid); free(L->pcol); free(L->pw);
     }
     free(H->lu); free(H->piv);

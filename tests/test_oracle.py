@@ -327,3 +327,41 @@ def test_bicgstab_with_air_matches_scipy_solution(sys2d):
     xs, info = spl.bicgstab(A, s.rhs, rtol=1e-13, maxiter=20000)
     assert info == 0
     assert np.linalg.norm(x - xs) <= 1e-8 * np.linalg.norm(xs)
+
+
+# ---------------------------------------------------- the paper's threshold pair
+def test_theta_pair_equal_thresholds_is_the_single_threshold_setup(sys2d):
+    s = sys2d
+    H1 = oracle.setup(s.row_ptr, s.col, s.val, theta=0.25, max_coarse=100)
+    H2 = oracle.setup(s.row_ptr, s.col, s.val, theta=0.25, theta_r=0.25, max_coarse=100)
+    assert len(H1.levels) == len(H2.levels)
+    for L1, L2 in zip(H1.levels, H2.levels):
+        assert np.array_equal(L1.A[2], L2.A[2])
+        if L1.R is not None:
+            assert np.array_equal(L1.R[1], L2.R[1]) and np.array_equal(L1.R[2], L2.R[2])
+
+
+def test_theta_pair_r_uses_its_own_strength_graph(sys2d):
+    """Section 4: coarsening at strength 0.2, R from distance-one
+    neighbourhoods at strength 0.3.  The splitting and P are those of the 0.2
+    setup; every R row is {i} plus the F points strong for i at 0.3 (the
+    classical definition, recomputed here from the matrix)."""
+    s = sys2d
+    Hc = oracle.setup(s.row_ptr, s.col, s.val, theta=0.2, max_coarse=100)
+    H = oracle.setup(s.row_ptr, s.col, s.val, theta=0.2, theta_r=0.3, max_coarse=100)
+    L, Lc = H.levels[0], Hc.levels[0]
+    assert np.array_equal(L.cf, Lc.cf) and np.array_equal(L.pcol, Lc.pcol)
+    rp, ci, v = L.A
+    Rp, Rc = L.R[0], L.R[1]
+    C = np.nonzero(L.cf == 1)[0]
+    differs = 0
+    for r, i in enumerate(C):
+        cols, vals = ci[rp[i]:rp[i + 1]], np.abs(v[rp[i]:rp[i + 1]])
+        off = cols != i
+        mx = vals[off].max() if off.any() else 0.0
+        strong = cols[off & (vals >= 0.3 * mx)] if mx > 0 else np.array([], dtype=cols.dtype)
+        want = np.sort(np.concatenate([[i], strong[L.cf[strong] == 0]]))
+        got = Rc[Rp[r]:Rp[r + 1]]
+        assert np.array_equal(got, want)
+        differs += len(got) != Lc.R[0][r + 1] - Lc.R[0][r]
+    assert differs > 0                      # the thresholds really select different neighbourhoods
