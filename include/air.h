@@ -69,6 +69,8 @@ typedef struct {
     int restart;         /* GMRES restart length m (<= 32) */
     int max_iter;        /* total inner GMRES steps */
     int validate;        /* 1: check the CSR before setup (one extra pass) */
+    double theta_r;      /* strength threshold of R's l-AIR neighbourhoods; < 0: theta (Section 4
+                            uses 0.3 for R with 0.2 for the coarsening) */
 } air_options;
 
 typedef struct {
@@ -93,7 +95,7 @@ typedef struct air_hierarchy air_hierarchy;   /* opaque, library-owned */
 
 /* Fill *opt with the defaults: theta 0.25, distance 1, relax "FCF", omega 1,
  * max_coarse 1000, max_levels 25, max_dense 4096, AIR_PREC_F64, restart 30,
- * max_iter 1000, validate 1. */
+ * max_iter 1000, validate 1, theta_r -1 (same as theta). */
 void air_default_options(air_options *opt);
 
 /* Build the l-AIR hierarchy of A (Section 3; Section 4 solver settings):

@@ -201,9 +201,20 @@ int coarsen(air_hierarchy *H, int l, cudaStream_t s, int *stop) {
     L.nf = n - nc;
     AIR_TRY(dalloc(&L.frows, L.nf));
     AIR_TRY(air_point_list(n, L.cf, 0, L.frows, scanw, s));
-    // a4 l-AIR restriction
+    // a4 l-AIR restriction, from its own strength graph when its threshold differs
     T.start(3);
-    AIR_TRY(air_lair_counts(nc, L.crows, L.srp, L.sci, L.cf, cnt, s));
+    int64_t *rsrp = nullptr;
+    int32_t *rsci = nullptr;
+    if (o.theta_r >= 0.0 && o.theta_r != o.theta) {
+        AIR_TRY(dalloc(&rsrp, n + 1));
+        AIR_TRY(air_strength(L, o.theta_r, nullptr, nullptr, cnt, 0, s));
+        AIR_TRY(air_exclusive_scan_i32(cnt, rsrp, n, s));
+        int64_t nnz_sr = 0;
+        AIR_TRY(read_i64(rsrp + n, &nnz_sr, s));
+        AIR_TRY(dalloc(&rsci, nnz_sr));
+        AIR_TRY(air_strength(L, o.theta_r, rsrp, rsci, nullptr, 1, s));
+    }
+    AIR_TRY(air_lair_counts(nc, L.crows, rsrp ? rsrp : L.srp, rsrp ? rsci : L.sci, L.cf, cnt, s));
     AIR_TRY(dalloc(&L.rrp, nc + 1));
     AIR_TRY(air_exclusive_scan_i32(cnt, L.rrp, nc, s));
     AIR_CUDA(cudaMemsetAsync(dmax, 0, sizeof(int32_t), s));
@@ -217,9 +228,16 @@ int coarsen(air_hierarchy *H, int l, cudaStream_t s, int *stop) {
     int64_t *dsing = nullptr;
     AIR_TRY(dalloc(&dsing, 1));
     AIR_CUDA(cudaMemsetAsync(dsing, 0, sizeof(int64_t), s));
-    AIR_TRY(air_lair_solve(L, L.max_m, dsing, s));
+    AirLevel LS = L;            // the level with R's strength graph in place of the coarsening one
+    if (rsrp) {
+        LS.srp = rsrp;
+        LS.sci = rsci;
+    }
+    AIR_TRY(air_lair_solve(LS, L.max_m, dsing, s));
     AIR_TRY(read_i64(dsing, &L.n_singular, s));
     dfree(dsing);
+    dfree(rsrp);
+    dfree(rsci);
     // a5 one-point interpolation
     T.start(4);
     AIR_TRY(dalloc(&L.pcol, n));
@@ -558,6 +576,7 @@ void air_default_options(air_options *o) {
     o->restart = 30;
     o->max_iter = 1000;
     o->validate = 1;
+    o->theta_r = -1.0;
 }
 
 int air_setup(const air_csr *A, double theta, int distance, const air_options *opt, void *stream,
@@ -574,7 +593,7 @@ int air_setup(const air_csr *A, double theta, int distance, const air_options *o
     o.relax[sizeof(o.relax) - 1] = 0;
     for (const char *c = o.relax; *c; ++c)
         if (*c != 'F' && *c != 'C') return AIR_ERR_INVALID_ARG;
-    if (!(theta >= 0.0) || !(theta <= 1.0) || o.max_levels < 1 || o.max_levels > AIR_MAX_LEVELS ||
+    if (!(theta >= 0.0) || !(theta <= 1.0) || !(o.theta_r <= 1.0) || o.max_levels < 1 || o.max_levels > AIR_MAX_LEVELS ||
         o.max_dense < 1 || o.restart < 1 || o.restart > 32 || o.max_iter < 0 ||
         (o.precision != AIR_PREC_F64 && o.precision != AIR_PREC_F32 && o.precision != AIR_PREC_BF16))
         return AIR_ERR_INVALID_ARG;
