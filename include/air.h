@@ -136,6 +136,25 @@ int air_spmv(const air_csr *A, const double *x, double *y, void *stream);
 int air_bicgstab_solve(const air_csr *A, const air_hierarchy *H, const double *b, double *x, double rtol,
                        void *stream, air_solve_info *info);
 
+/* Many right-hand sides through one hierarchy.  b and x are device arrays
+ * of n x k doubles, row-major (the k values of row i are contiguous), k in
+ * 1 .. 32.  The matrix traffic of a V-cycle is shared by the k systems: one
+ * warp per matrix row, one lane per system.
+ *
+ * air_vcycle_multi: x = M^{-1} b column by column, the FP64 V-cycle of H
+ * (whatever H's storage precision), summed in the same order as air_vcycle's
+ * FP64 form.  Asynchronous on the stream.
+ *
+ * air_bicgstab_solve_multi: air_bicgstab_solve on the k systems A x_j = b_j
+ * in lockstep, with the FP64 V-cycle as preconditioner: each column has its
+ * own scalars and stopping test and is frozen once converged; info[j] (k
+ * entries) reports column j.  Returns AIR_NOT_CONVERGED if any column did not
+ * converge.  Device buffers only.  The paper solves one right-hand side at a
+ * time. */
+int air_vcycle_multi(const air_hierarchy *H, int k, const double *b, double *x, void *stream);
+int air_bicgstab_solve_multi(const air_csr *A, const air_hierarchy *H, int k, const double *b, double *x,
+                             double rtol, void *stream, air_solve_info *info);
+
 /* Independent problems at once.  The paper solves one system at a time;
  * these run count independent setups (or solves) concurrently, one host
  * thread and one stream per problem (streams[k], or a library-created stream

@@ -25,7 +25,7 @@ EXPORTED = ["air_default_options", "air_setup", "air_vcycle", "air_spmv", "air_g
             "air_hierarchy_levels", "air_hierarchy_info", "air_hierarchy_export", "air_free",
             "air_status_string", "air_kernel_launches", "air_gmres_solve_noalloc", "air_setup_timings",
             "air_csr_transpose", "air_csr_outer", "air_setup_batch", "air_gmres_solve_batch",
-            "air_bicgstab_solve"]
+            "air_bicgstab_solve", "air_vcycle_multi", "air_bicgstab_solve_multi"]
 
 
 class air_csr(C.Structure):
@@ -105,6 +105,11 @@ def lib() -> C.CDLL:
     L.air_bicgstab_solve.argtypes = [C.POINTER(air_csr), C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
                                      C.c_void_p, C.POINTER(air_solve_info)]
     L.air_bicgstab_solve.restype = C.c_int
+    L.air_vcycle_multi.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
+    L.air_vcycle_multi.restype = C.c_int
+    L.air_bicgstab_solve_multi.argtypes = [C.POINTER(air_csr), C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
+                                           C.c_double, C.c_void_p, C.POINTER(air_solve_info)]
+    L.air_bicgstab_solve_multi.restype = C.c_int
     L.air_setup_batch.argtypes = [C.c_int, C.POINTER(air_csr), C.c_double, C.c_int, C.POINTER(air_options),
                                   C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.POINTER(C.c_int)]
     L.air_setup_batch.restype = C.c_int
@@ -443,3 +448,28 @@ def gmres_solve_batch(As, Hs, bs, xs=None, rtol: float = 1e-8, streams=None):
     if r < 0 and all(int(x) >= 0 for x in st):
         _check(r, "air_gmres_solve_batch")
     return xs, [inf[i] for i in range(k)], [int(x) for x in st]
+
+
+# ------------------------------------------------------- many right-hand sides
+def vcycle_multi(H: Hierarchy, B, X=None, stream=None):
+    """air_vcycle_multi: X = M^{-1} B for an (n, k) row-major FP64 device tensor, k <= 32."""
+    import torch
+    if X is None:
+        X = torch.empty_like(B)
+    _check(lib().air_vcycle_multi(H.handle, int(B.shape[1]), C.c_void_p(B.data_ptr()), C.c_void_p(X.data_ptr()),
+                                  C.c_void_p(_stream(stream))), "air_vcycle_multi")
+    return X
+
+
+def bicgstab_solve_multi(A: CSR, H: Hierarchy, B, X=None, rtol: float = 1e-12, stream=None):
+    """air_bicgstab_solve_multi on the columns of an (n, k) FP64 device tensor.  Returns (X, infos)."""
+    import torch
+    k = int(B.shape[1])
+    if X is None:
+        X = torch.empty_like(B)
+    inf = (air_solve_info * k)()
+    Ac = A.c()
+    st = lib().air_bicgstab_solve_multi(C.byref(Ac), H.handle, k, C.c_void_p(B.data_ptr()),
+                                        C.c_void_p(X.data_ptr()), float(rtol), C.c_void_p(_stream(stream)), inf)
+    _check(st, "air_bicgstab_solve_multi")
+    return X, [inf[j] for j in range(k)]

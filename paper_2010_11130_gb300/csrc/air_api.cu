@@ -643,6 +643,21 @@ int air_bicgstab_solve(const air_csr *A, const air_hierarchy *H, const double *b
     return st;
 }
 
+int air_vcycle_multi(const air_hierarchy *H, int k, const double *b, double *x, void *stream) {
+    if (!H || !b || !x || k < 1 || k > 32) return AIR_ERR_INVALID_ARG;
+    AirCallStream call((cudaStream_t)stream);
+    return air_vcycle_multi_run(H, k, b, x, (cudaStream_t)stream);
+}
+
+int air_bicgstab_solve_multi(const air_csr *A, const air_hierarchy *H, int k, const double *b, double *x,
+                             double rtol, void *stream, air_solve_info *info) {
+    if (!A || !H || !b || !x || !info || k < 1 || k > 32 || !(rtol > 0.0) || !A->on_device ||
+        A->n_rows != H->lev[0].n)
+        return AIR_ERR_INVALID_ARG;
+    AirCallStream call((cudaStream_t)stream);
+    return air_bicgstab_multi_impl(H, k, b, x, rtol, (cudaStream_t)stream, info);
+}
+
 int air_csr_transpose(const air_csr *A, int64_t *row_ptr_t, int32_t *col_t, double *val_t, void *stream) {
     if (!A || !row_ptr_t || !A->on_device || A->n_rows < 0 || A->n_cols < 0 || A->nnz < 0 || !A->row_ptr)
         return AIR_ERR_INVALID_ARG;
@@ -749,6 +764,7 @@ void air_free(air_hierarchy *H) {
     if (cur != H->dev) cudaSetDevice(H->dev);
     cudaDeviceSynchronize();
     for (int l = 0; l < AIR_MAX_LEVELS; ++l) free_level(H->lev[l]);
+    air_free_multi(H);
     air_free_sell(H->a0);
     if (H->vgraph) cudaGraphExecDestroy(H->vgraph);
     H->vgraph = nullptr;

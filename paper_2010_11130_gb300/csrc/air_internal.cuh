@@ -152,6 +152,13 @@ struct air_hierarchy {
     double *scal = nullptr;           // [0] norm, [1] estimate, ...
     double *h_est = nullptr;          // pinned host mirror of scalars
     double *xd = nullptr, *bd = nullptr;  // device b and x when the caller passes host vectors
+    // many right-hand sides (allocated on first use): per level, b, x and a
+    // compact sweep buffer of n_l x mk row-major FP64; the Krylov vectors of
+    // the lockstep solve
+    int mk = 0;
+    double *mb[AIR_MAX_LEVELS] = {}, *mx[AIR_MAX_LEVELS] = {}, *mt[AIR_MAX_LEVELS] = {};
+    double *mkry = nullptr;
+    size_t mkry_n = 0;
 };
 
 // ------------------------------------------------------------------ launchers
@@ -191,6 +198,12 @@ int air_csr_transpose_impl(int64_t n, int64_t ncols, int64_t nnz, const int64_t 
                            const double *v, int64_t *rpt, int32_t *cit, double *vt, int *d_err, cudaStream_t s);
 int air_csr_outer_impl(int64_t n, int64_t ncols, const int64_t *rp, const int32_t *ci, const double *u,
                        const double *w, double alpha, double *out, cudaStream_t s);
+
+// multi_rhs.cu: k <= 32 right-hand sides, row-major n x k FP64
+int air_vcycle_multi_run(const air_hierarchy *H, int k, const double *b, double *x, cudaStream_t s);
+int air_bicgstab_multi_impl(const air_hierarchy *H, int k, const double *b, double *x, double rtol,
+                            cudaStream_t s, air_solve_info *info);
+void air_free_multi(air_hierarchy *H);
 
 // solve_kernels.cu
 // y = A x, or y = b - A x if b != NULL; nnz < 0 / maxrow <= 0 when unknown
