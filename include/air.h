@@ -145,13 +145,20 @@ int air_bicgstab_solve(const air_csr *A, const air_hierarchy *H, const double *b
  * (whatever H's storage precision), summed in the same order as air_vcycle's
  * FP64 form.  Asynchronous on the stream.
  *
+ * air_vcycle_multi_f32: the same with float b and x on round-to-nearest
+ * FP32 copies of the hierarchy's operators (made on first use), summed in the
+ * order of air_vcycle's FP32 form.  The FP32 FMA rate of GB300 is many times
+ * its FP64 rate, and k systems per matrix entry make the FP64 form ALU-bound.
+ *
  * air_bicgstab_solve_multi: air_bicgstab_solve on the k systems A x_j = b_j
- * in lockstep, with the FP64 V-cycle as preconditioner: each column has its
- * own scalars and stopping test and is frozen once converged; info[j] (k
- * entries) reports column j.  Returns AIR_NOT_CONVERGED if any column did not
+ * in lockstep, preconditioned by the multi V-cycle in H's precision (FP64 for
+ * an FP64 hierarchy, FP32 for FP32 and BF16 storage): each column has its own
+ * scalars and stopping test and is frozen once converged; info[j] (k entries)
+ * reports column j.  Returns AIR_NOT_CONVERGED if any column did not
  * converge.  Device buffers only.  The paper solves one right-hand side at a
  * time. */
 int air_vcycle_multi(const air_hierarchy *H, int k, const double *b, double *x, void *stream);
+int air_vcycle_multi_f32(const air_hierarchy *H, int k, const float *b, float *x, void *stream);
 int air_bicgstab_solve_multi(const air_csr *A, const air_hierarchy *H, int k, const double *b, double *x,
                              double rtol, void *stream, air_solve_info *info);
 

@@ -25,7 +25,8 @@ EXPORTED = ["air_default_options", "air_setup", "air_vcycle", "air_spmv", "air_g
             "air_hierarchy_levels", "air_hierarchy_info", "air_hierarchy_export", "air_free",
             "air_status_string", "air_kernel_launches", "air_gmres_solve_noalloc", "air_setup_timings",
             "air_csr_transpose", "air_csr_outer", "air_setup_batch", "air_gmres_solve_batch",
-            "air_bicgstab_solve", "air_vcycle_multi", "air_bicgstab_solve_multi"]
+            "air_bicgstab_solve", "air_vcycle_multi", "air_bicgstab_solve_multi",
+            "air_vcycle_multi_f32"]
 
 
 class air_csr(C.Structure):
@@ -107,6 +108,8 @@ def lib() -> C.CDLL:
     L.air_bicgstab_solve.restype = C.c_int
     L.air_vcycle_multi.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
     L.air_vcycle_multi.restype = C.c_int
+    L.air_vcycle_multi_f32.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
+    L.air_vcycle_multi_f32.restype = C.c_int
     L.air_bicgstab_solve_multi.argtypes = [C.POINTER(air_csr), C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
                                            C.c_double, C.c_void_p, C.POINTER(air_solve_info)]
     L.air_bicgstab_solve_multi.restype = C.c_int
@@ -452,12 +455,14 @@ def gmres_solve_batch(As, Hs, bs, xs=None, rtol: float = 1e-8, streams=None):
 
 # ------------------------------------------------------- many right-hand sides
 def vcycle_multi(H: Hierarchy, B, X=None, stream=None):
-    """air_vcycle_multi: X = M^{-1} B for an (n, k) row-major FP64 device tensor, k <= 32."""
+    """air_vcycle_multi (float64 B) or air_vcycle_multi_f32 (float32 B): X = M^{-1} B
+    for an (n, k) row-major device tensor, k <= 32."""
     import torch
     if X is None:
         X = torch.empty_like(B)
-    _check(lib().air_vcycle_multi(H.handle, int(B.shape[1]), C.c_void_p(B.data_ptr()), C.c_void_p(X.data_ptr()),
-                                  C.c_void_p(_stream(stream))), "air_vcycle_multi")
+    fn = lib().air_vcycle_multi_f32 if B.dtype == torch.float32 else lib().air_vcycle_multi
+    _check(fn(H.handle, int(B.shape[1]), C.c_void_p(B.data_ptr()), C.c_void_p(X.data_ptr()),
+              C.c_void_p(_stream(stream))), "air_vcycle_multi")
     return X
 
 

@@ -649,6 +649,12 @@ int air_vcycle_multi(const air_hierarchy *H, int k, const double *b, double *x, 
     return air_vcycle_multi_run(H, k, b, x, (cudaStream_t)stream);
 }
 
+int air_vcycle_multi_f32(const air_hierarchy *H, int k, const float *b, float *x, void *stream) {
+    if (!H || !b || !x || k < 1 || k > 32) return AIR_ERR_INVALID_ARG;
+    AirCallStream call((cudaStream_t)stream);
+    return air_vcycle_multi_run_f32(H, k, b, x, (cudaStream_t)stream);
+}
+
 int air_bicgstab_solve_multi(const air_csr *A, const air_hierarchy *H, int k, const double *b, double *x,
                              double rtol, void *stream, air_solve_info *info) {
     if (!A || !H || !b || !x || !info || k < 1 || k > 32 || !(rtol > 0.0) || !A->on_device ||

@@ -159,6 +159,10 @@ struct air_hierarchy {
     double *mb[AIR_MAX_LEVELS] = {}, *mx[AIR_MAX_LEVELS] = {}, *mt[AIR_MAX_LEVELS] = {};
     double *mkry = nullptr;
     size_t mkry_n = 0;
+    // FP32 copies for the FP32 multi V-cycle: A_l values, 1 / a_ii, R_l values, coarsest inverse
+    int m32 = 0;
+    float *mv32[AIR_MAX_LEVELS] = {}, *md32[AIR_MAX_LEVELS] = {}, *mr32[AIR_MAX_LEVELS] = {};
+    float *mc32 = nullptr;
 };
 
 // ------------------------------------------------------------------ launchers
@@ -201,6 +205,7 @@ int air_csr_outer_impl(int64_t n, int64_t ncols, const int64_t *rp, const int32_
 
 // multi_rhs.cu: k <= 32 right-hand sides, row-major n x k FP64
 int air_vcycle_multi_run(const air_hierarchy *H, int k, const double *b, double *x, cudaStream_t s);
+int air_vcycle_multi_run_f32(const air_hierarchy *H, int k, const float *b, float *x, cudaStream_t s);
 int air_bicgstab_multi_impl(const air_hierarchy *H, int k, const double *b, double *x, double rtol,
                             cudaStream_t s, air_solve_info *info);
 void air_free_multi(air_hierarchy *H);

@@ -95,3 +95,32 @@ def test_multi_rejects_bad_k():
     with pytest.raises(air.AirError) as e:
         air.vcycle_multi(H, torch.zeros((s.n, 33), dtype=torch.float64, device="cuda"))
     assert e.value.status == -1
+
+
+@pytest.mark.parametrize("name", list(_CASES))
+def test_vcycle_multi_f32_matches_single_fp32_vcycles(name):
+    s = _system(name)
+    A = air.CSR.from_host(s.row_ptr, s.col, s.val)
+    H = air.setup(A, theta=0.25, max_coarse=100, precision=1)
+    k = 8
+    B = _columns(s, k)
+    X = air.vcycle_multi(H, torch.from_numpy(B).float().cuda()).double().cpu().numpy()
+    for j in range(k):
+        xj = H.vcycle(torch.from_numpy(np.ascontiguousarray(B[:, j])).cuda()).cpu().numpy()
+        assert np.linalg.norm(X[:, j] - xj) <= 1e-5 * np.linalg.norm(xj), j
+
+
+def test_bicgstab_multi_fp32_preconditioner():
+    s = _system("st2d_n6_p2_nu1e-6")
+    A = air.CSR.from_host(s.row_ptr, s.col, s.val)
+    H = air.setup(A, theta=0.25, max_coarse=100, precision=1)
+    k = 4
+    B = _columns(s, k)
+    X, infos = air.bicgstab_solve_multi(A, H, torch.from_numpy(B).cuda(), rtol=1e-10)
+    X = X.cpu().numpy()
+    for j in range(k):
+        b = np.ascontiguousarray(B[:, j])
+        _, i1 = air.bicgstab_solve(A, H, torch.from_numpy(b).cuda(), rtol=1e-10)
+        assert infos[j].status == 0 and abs(infos[j].iters - i1.iters) <= 2, (j, infos[j].iters, i1.iters)
+        r = b - oracle.spmv(s.row_ptr, s.col, s.val, X[:, j])
+        assert np.linalg.norm(r) <= 1e-10 * np.linalg.norm(b) * (1 + 1e-6)
