@@ -92,19 +92,18 @@ void free_workspace(air_hierarchy *H) {
 }
 
 // First-pass kernel variant: 4 (default, fastest measured) per-bucket
-// cursors in shared memory, fixed-size two-hop lines and fire-and-forget
-// bitmap updates, two dependent round trips per pick (levels outside its
-// limits take 2); 2 exact bitmaps, two-hop lists and int8 measures with
-// warp-combined read-modify-writes; 3 one round trip of loads per pick with
-// atomic bitmap updates; 1 lazy bitmaps with L1-cached loads; 0 lazy bitmaps
-// with L2-only loads.  All give the same splitting.  Set by the environment
-// variable AIR_RS_VARIANT.
+// cursors in shared memory, deduplicated neighbourhood blocks and
+// fire-and-forget bitmap updates, two dependent round trips per pick (levels
+// outside its limits take 2); 2 exact bitmaps, two-hop lists and int8 measures
+// with warp-combined read-modify-writes (measures up to 124); 1 lazy bitmaps
+// with L1-cached loads and 0 lazy bitmaps with L2-only loads (int32 measures,
+// the fallback for any level).  All give the same splitting.  Set by the
+// environment variable AIR_RS_VARIANT (read once).
 int rs_cached() {
-    static int v = -1;
-    if (v < 0) {
+    static const int v = [] {
         const char *e = getenv("AIR_RS_VARIANT");
-        v = (e && e[0] >= '0' && e[0] <= '4') ? e[0] - '0' : 4;
-    }
+        return (e && (e[0] == '0' || e[0] == '1' || e[0] == '2' || e[0] == '4')) ? e[0] - '0' : 4;
+    }();
     return v;
 }
 

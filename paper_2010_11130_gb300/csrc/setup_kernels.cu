@@ -597,279 +597,6 @@ __global__ void rs3_finish_kernel(int64_t n, const int8_t *lam, int8_t *cf) {
         cf[i] = lam[i] == L8_C ? 1 : 0;
 }
 
-// ------------------------------------ first pass, one-round-trip version (v4)
-// The same sequential first pass.  Per pick it loads the point's whole
-// two-hop list (S^T_i, each S_j, S_i; kept in a fixed 256-byte slot per point
-// so the next likely pick can be prefetched) and the measures of every listed
-// point in one round trip each, then computes all consequences in registers
-// and issues the stores and bitmap updates without waiting for them
-// (red.and / red.or).  Leaf bitmap words are exact, so the lowest set bit of
-// the top bucket is always the next pick; the level-1 and level-2 summaries
-// are only ever set by updates and are cleared lazily by the search.
-constexpr int V4_LINE = 32;   // uint64 words per point: header + 31 inline entries
-constexpr int V4_INLINE = V4_LINE - 1;
-
-struct RS4Args {
-    int64_t n;
-    const unsigned long long *lines;   // n * V4_LINE
-    const int64_t *ovf_ptr;            // overflow entries of point i start here (count > V4_INLINE)
-    const unsigned long long *ovf;
-    int8_t *lam;
-    uint64_t *L0, *L1, *L2;
-    int64_t w0, w1, w2;
-    int nb, top, ent_cap;
-    int64_t cap;
-    int *err;
-    unsigned long long *stats;     // [0] picks, [1] search iterations, [2] general-path picks
-};
-
-__global__ void hop4_fill_kernel(int64_t n, const int64_t *srp, const int32_t *sci, const int64_t *strp,
-                                 const int32_t *stci, const int32_t *cnt, const int64_t *ovf_ptr,
-                                 unsigned long long *lines, unsigned long long *ovf) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        unsigned long long *line = lines + i * V4_LINE;
-        unsigned long long *of = ovf + ovf_ptr[i];
-        int64_t c = strp[i + 1] - strp[i];
-        line[0] = (unsigned long long)(unsigned)cnt[i] | ((unsigned long long)c << 32);
-        int64_t e = 0;
-        auto put = [&](unsigned long long v) {
-            if (e < V4_INLINE) line[1 + e] = v; else of[e - V4_INLINE] = v;
-            ++e;
-        };
-        for (int64_t q = strp[i]; q < strp[i + 1]; ++q) put(((unsigned long long)TAG_J << 32) | (unsigned)stci[q]);
-        uint32_t t = 0;
-        for (int64_t q = strp[i]; q < strp[i + 1]; ++q, ++t) {
-            int32_t j = stci[q];
-            for (int64_t r = srp[j]; r < srp[j + 1]; ++r) put(((unsigned long long)t << 32) | (unsigned)sci[r]);
-        }
-        for (int64_t r = srp[i]; r < srp[i + 1]; ++r) put(((unsigned long long)TAG_SI << 32) | (unsigned)sci[r]);
-    }
-}
-
-__global__ void ovf_count_kernel(int64_t n, const int32_t *cnt, int32_t *ocnt) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        ocnt[i] = cnt[i] > V4_INLINE ? cnt[i] - V4_INLINE : 0;
-}
-
-// Exact bitmap maintenance with returning atomics: a removal that empties a
-// leaf word clears its level-1 bit (and so on up); an insertion into an empty
-// word sets it.  All removals of a pick run before all its insertions (a
-// barrier between them), so a word's emptying and refilling never race.
-__device__ __forceinline__ void rs4_remove(const RS4Args &a, uint64_t *L2s, int b, int64_t k) {
-    const uint64_t bit = 1ull << (k & 63);
-    const uint64_t o0 = atomicAnd((unsigned long long *)&a.L0[(int64_t)b * a.w0 + (k >> 6)], (unsigned long long)~bit);
-    if ((o0 & ~bit) == 0ull) {
-        const int64_t i1 = k >> 6;
-        const uint64_t b1 = 1ull << (i1 & 63);
-        const uint64_t o1 = atomicAnd((unsigned long long *)&a.L1[(int64_t)b * a.w1 + (i1 >> 6)], (unsigned long long)~b1);
-        if ((o1 & ~b1) == 0ull) {
-            const int64_t i2 = i1 >> 6;
-            atomicAnd((unsigned long long *)&L2s[(int64_t)b * a.w2 + (i2 >> 6)], (unsigned long long)~(1ull << (i2 & 63)));
-        }
-    }
-}
-
-__device__ __forceinline__ void rs4_insert(const RS4Args &a, uint64_t *L2s, int b, int64_t k) {
-    const uint64_t o0 = atomicOr((unsigned long long *)&a.L0[(int64_t)b * a.w0 + (k >> 6)], (unsigned long long)(1ull << (k & 63)));
-    if (o0 == 0ull) {
-        const int64_t i1 = k >> 6;
-        const uint64_t o1 = atomicOr((unsigned long long *)&a.L1[(int64_t)b * a.w1 + (i1 >> 6)],
-                                     (unsigned long long)(1ull << (i1 & 63)));
-        if (o1 == 0ull) {
-            const int64_t i2 = i1 >> 6;
-            atomicOr((unsigned long long *)&L2s[(int64_t)b * a.w2 + (i2 >> 6)], (unsigned long long)(1ull << (i2 & 63)));
-        }
-    }
-}
-
-// Next pick: lowest set bit of the highest non-empty bucket.  Returns the
-// point (and its leaf word in *l0w, its index in *i0w), -1 when no bucket
-// >= 1 is left, -2 on the iteration cap.
-__device__ int64_t rs4_search(const RS4Args &a, uint64_t *L2s, int *top, int64_t *iters, uint64_t *l0w,
-                              int64_t *i0w) {
-    int lane = threadIdx.x & 31;
-    int b = *top;
-    while (true) {
-        if (b < 1) { *top = 0; return -1; }
-        if (++(*iters) > a.cap) return -2;
-        int64_t w = -1;
-        for (int64_t base = 0; base < a.w2; base += 32) {
-            uint64_t val = (base + lane < a.w2) ? L2s[(int64_t)b * a.w2 + base + lane] : 0ull;
-            unsigned bal = __ballot_sync(FULL, val != 0ull);
-            if (bal) { w = base + __ffs(bal) - 1; break; }
-        }
-        if (w < 0) { --b; continue; }
-        int64_t res = -3;
-        uint64_t l0 = 0;
-        int64_t i0 = 0;
-        if (lane == 0) {
-            uint64_t *p2 = &L2s[(int64_t)b * a.w2 + w];
-            uint64_t l2 = *p2;
-            int bit2 = __ffsll((long long)l2) - 1;
-            int64_t i1 = w * 64 + bit2;
-            uint64_t *p1 = &a.L1[(int64_t)b * a.w1 + i1];
-            uint64_t l1 = __ldcg((const unsigned long long *)p1);
-            res = -2;                          // an empty summarised word would be an inconsistency
-            if (l1 != 0ull) {
-                int bit1 = __ffsll((long long)l1) - 1;
-                i0 = i1 * 64 + bit1;
-                l0 = __ldcg((const unsigned long long *)&a.L0[(int64_t)b * a.w0 + i0]);
-                if (l0 != 0ull) res = i0 * 64 + (__ffsll((long long)l0) - 1);
-            }
-        }
-        res = __shfl_sync(FULL, res, 0);
-        __syncwarp();
-        if (res == -2) return -2;
-        if (res >= 0) {
-            *top = b;
-            *l0w = __shfl_sync(FULL, l0, 0);
-            *i0w = __shfl_sync(FULL, i0, 0);
-            return res;
-        }
-    }
-}
-
-__global__ void __launch_bounds__(32) rs4_warp_kernel(RS4Args a) {
-    extern __shared__ uint64_t smem[];
-    uint64_t *L2s = smem;                                             // nb * w2
-    unsigned long long *ent = (unsigned long long *)(L2s + (int64_t)a.nb * a.w2);   // ent_cap
-    int8_t *lvs = (int8_t *)(ent + a.ent_cap);                        // ent_cap
-    int8_t *nvs = lvs + a.ent_cap;                                    // ent_cap
-    const int lane = threadIdx.x & 31;
-    for (int64_t t = lane; t < (int64_t)a.nb * a.w2; t += 32) L2s[t] = a.L2[t];
-    int top = a.top;
-    int64_t iters = 0;
-    unsigned long long slow = 0;
-    __syncwarp();
-    for (int64_t pick_no = 0; pick_no <= a.n; ++pick_no) {
-        uint64_t l0 = 0;
-        int64_t i0 = 0;
-        const int64_t i = rs4_search(a, L2s, &top, &iters, &l0, &i0);
-        if (i < 0) {
-            if (i == -2 && lane == 0) atomicOr(a.err, AIR_DEVERR_RS_CAP);
-            if (lane == 0) { a.stats[0] += (unsigned long long)pick_no; a.stats[1] += (unsigned long long)iters; a.stats[2] += slow; }
-            break;
-        }
-        const int b = top;
-        // prefetch the slot of the next set bit of the same word (the likely next pick)
-        if (lane < 2) {
-            uint64_t rest = l0 & (l0 - 1);
-            if (rest) {
-                int64_t nxt = i0 * 64 + (__ffsll((long long)rest) - 1);
-                const void *p = a.lines + nxt * V4_LINE + lane * 16;
-                asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-            }
-        }
-        // this pick's list: header in lane 0, entries 0..30 in lanes 1..31
-        const unsigned long long word = __ldcg(a.lines + i * V4_LINE + lane);
-        const unsigned long long hdr = __shfl_sync(FULL, word, 0);
-        const int cnt = (int)(unsigned)hdr;
-        const int c = (int)(hdr >> 32);
-        if (lane == 0) a.lam[i] = L8_C;
-        __syncwarp();
-        int vmax = 0;
-        if (cnt <= V4_INLINE) {
-            // ---- fast path: one entry per lane
-            const unsigned long long e = __shfl_down_sync(FULL, word, 1);
-            const bool valid = lane < cnt;
-            const int32_t k = (int32_t)(unsigned)e;
-            const uint32_t tag = (uint32_t)(e >> 32);
-            const bool isJ = valid && lane < c;
-            const int lv = valid ? (int)__ldcg(&a.lam[k]) : -3;
-            const bool newF = isJ && lv >= 0;
-            const int jsrc = (valid && !isJ && tag != TAG_SI) ? (int)tag : lane;
-            const bool jnew = __shfl_sync(FULL, newF, jsrc);
-            const int delta = (!valid || isJ) ? 0 : (tag == TAG_SI ? -1 : (jnew ? 1 : 0));
-            const unsigned m = __match_any_sync(FULL, valid ? k : -1);
-            const unsigned anyF = __reduce_or_sync(m, newF ? 1u : 0u);
-            const int sum = __reduce_add_sync(m, delta);
-            const bool leader = valid && lane == __ffs(m) - 1;
-            const bool upd = leader && !anyF && lv >= 0 && sum != 0;
-            const int nv = lv + sum;
-            // removals: the pick (lane 31 is never a list entry here), new F points, moved points
-            if (lane == 31) rs4_remove(a, L2s, b, i);
-            if (newF) {
-                a.lam[k] = L8_F;
-                if (lv >= 1) rs4_remove(a, L2s, lv, k);
-            }
-            if (upd) {
-                a.lam[k] = (int8_t)nv;
-                if (lv >= 1) rs4_remove(a, L2s, lv, k);
-            }
-            __syncwarp();
-            if (upd && nv >= 1) {
-                rs4_insert(a, L2s, nv, k);
-                vmax = nv;
-            }
-        } else {
-            // ---- general path: entries staged in shared memory
-            ++slow;
-            if (cnt > a.ent_cap) {
-                if (lane == 0) atomicOr(a.err, AIR_DEVERR_RS_CAP);
-                break;
-            }
-            if (lane >= 1) ent[lane - 1] = word;
-            const int64_t op = a.ovf_ptr[i];
-            for (int q = lane; q < cnt - V4_INLINE; q += 32) ent[V4_INLINE + q] = __ldcg(a.ovf + op + q);
-            __syncwarp();
-            for (int q = lane; q < cnt; q += 32) {
-                lvs[q] = __ldcg(&a.lam[(int32_t)(unsigned)ent[q]]);
-                nvs[q] = -128;
-            }
-            __syncwarp();
-            if (lane == 0) rs4_remove(a, L2s, b, i);
-            for (int q = lane; q < c; q += 32) {
-                if (lvs[q] >= 0) {
-                    const int32_t j = (int32_t)(unsigned)ent[q];
-                    a.lam[j] = L8_F;
-                    if (lvs[q] >= 1) rs4_remove(a, L2s, lvs[q], j);
-                }
-            }
-            // new measures go to nvs[] (one slot per entry; -128 = unchanged)
-            for (int q = c + lane; q < cnt; q += 32) {
-                const int32_t k = (int32_t)(unsigned)ent[q];
-                const uint32_t tag = (uint32_t)(ent[q] >> 32);
-                const int lv = lvs[q];
-                const int delta = tag == TAG_SI ? -1 : (lvs[tag] >= 0 ? 1 : 0);
-                if (delta == 0 || lv < 0) continue;
-                bool skip = false;
-                for (int t = 0; t < c && !skip; ++t)
-                    skip = (int32_t)(unsigned)ent[t] == k && lvs[t] >= 0;
-                for (int t = c; t < q && !skip; ++t) {
-                    if ((int32_t)(unsigned)ent[t] != k) continue;
-                    const uint32_t tg = (uint32_t)(ent[t] >> 32);
-                    skip = tg == TAG_SI || lvs[tg] >= 0;          // an earlier contributing entry leads
-                }
-                if (skip) continue;
-                int sum = 0;
-                for (int t = q; t < cnt; ++t) {
-                    if ((int32_t)(unsigned)ent[t] != k) continue;
-                    const uint32_t tg = (uint32_t)(ent[t] >> 32);
-                    sum += tg == TAG_SI ? -1 : (lvs[tg] >= 0 ? 1 : 0);
-                }
-                if (sum != 0) {
-                    const int nv = lv + sum;
-                    a.lam[k] = (int8_t)nv;
-                    if (lv >= 1) rs4_remove(a, L2s, lv, k);
-                    nvs[q] = (int8_t)nv;
-                }
-            }
-            __syncwarp();
-            for (int q = c + lane; q < cnt; q += 32) {
-                const int nv = nvs[q];
-                if (nv >= 1) {
-                    rs4_insert(a, L2s, nv, (int32_t)(unsigned)ent[q]);
-                    if (nv > vmax) vmax = nv;
-                }
-            }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) vmax = max(vmax, __shfl_xor_sync(FULL, vmax, o));
-        if (vmax > top) top = vmax;
-        __syncwarp();
-    }
-}
-
 // -------------------------------------------------------------- coarse ids
 __global__ void cflag_kernel(int64_t n, const int8_t *cf, int32_t *flag) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -1303,75 +1030,6 @@ int air_transpose_pattern(int64_t n, int64_t nnz, const int64_t *srp, const int3
     return AIR_OK;
 }
 
-static int rs_first_pass_v4(int64_t n, const int64_t *srp, const int32_t *sci, const int64_t *strp,
-                            const int32_t *stci, int32_t max_st, int32_t max_s, int8_t *cf, int *d_err,
-                            unsigned long long *stats, cudaStream_t s) {
-    RS4Args a;
-    a.n = n;
-    a.stats = stats;
-    a.nb = 2 * max_st + 1;
-    if (a.nb < 2) a.nb = 2;
-    a.top = a.nb - 1;
-    a.w0 = (n + 63) / 64;
-    a.w1 = (a.w0 + 63) / 64;
-    a.w2 = (a.w1 + 63) / 64;
-    a.err = d_err;
-    a.ent_cap = max_st + (max_st + 1) * (max_s > 0 ? max_s : 1) + 64;
-    int32_t *cnt = nullptr, *ocnt = nullptr;
-    int64_t *ovf_ptr = nullptr;
-    AIR_CUDA(cudaMallocAsync(&cnt, (size_t)(n > 0 ? n : 1) * sizeof(int32_t), s));
-    AIR_CUDA(cudaMallocAsync(&ocnt, (size_t)(n > 0 ? n : 1) * sizeof(int32_t), s));
-    AIR_CUDA(cudaMallocAsync(&ovf_ptr, (size_t)(n + 1) * sizeof(int64_t), s));
-    hop_count_kernel<<<air_counted(grid_for(n, 256)), 256, 0, s>>>(n, srp, strp, stci, cnt);
-    ovf_count_kernel<<<air_counted(grid_for(n, 256)), 256, 0, s>>>(n, cnt, ocnt);
-    AIR_LAUNCH();
-    AIR_TRY(air_exclusive_scan_i32(ocnt, ovf_ptr, n, s));
-    int64_t novf = 0;
-    AIR_CUDA(cudaMemcpyAsync(&novf, ovf_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    AIR_CUDA(cudaStreamSynchronize(s));
-    unsigned long long *lines = nullptr, *ovf = nullptr;
-    AIR_CUDA(cudaMallocAsync(&lines, (size_t)(n > 0 ? n : 1) * V4_LINE * sizeof(unsigned long long), s));
-    AIR_CUDA(cudaMallocAsync(&ovf, (size_t)(novf > 0 ? novf : 1) * sizeof(unsigned long long), s));
-    hop4_fill_kernel<<<air_counted(grid_for(n, 256)), 256, 0, s>>>(n, srp, sci, strp, stci, cnt, ovf_ptr, lines, ovf);
-    AIR_LAUNCH();
-    // each pick raises the top bucket by < nb and every lazily cleared
-    // summary bit was set by one update: bound the search loop by both
-    a.cap = (n + 1) * (int64_t)(a.nb + 1) + 4 * (n + novf + (int64_t)V4_INLINE * n) + 4096;
-    a.lines = lines;
-    a.ovf_ptr = ovf_ptr;
-    a.ovf = ovf;
-    size_t words = (size_t)a.nb * (size_t)(a.w0 + a.w1 + a.w2);
-    uint64_t *bits = nullptr;
-    int8_t *lam = nullptr;
-    AIR_CUDA(cudaMallocAsync(&bits, words * sizeof(uint64_t), s));
-    AIR_CUDA(cudaMallocAsync(&lam, (size_t)(n > 0 ? n : 1), s));
-    AIR_CUDA(cudaMemsetAsync(bits, 0, words * sizeof(uint64_t), s));
-    a.L0 = bits;
-    a.L1 = bits + (size_t)a.nb * a.w0;
-    a.L2 = a.L1 + (size_t)a.nb * a.w1;
-    a.lam = lam;
-    RS3Args i3{};
-    i3.n = n; i3.srp = srp; i3.strp = strp; i3.lam = lam; i3.L0 = a.L0; i3.L1 = a.L1; i3.L2 = a.L2;
-    i3.w0 = a.w0; i3.w1 = a.w1; i3.w2 = a.w2;
-    rs3_init_kernel<<<air_counted(grid_for(n, 256)), 256, 0, s>>>(i3);
-    AIR_LAUNCH();
-    size_t smem = (size_t)a.nb * a.w2 * sizeof(uint64_t) + (size_t)a.ent_cap * (sizeof(unsigned long long) + 2) + 16;
-    if (smem > AIR_SMEM_OPTIN) return AIR_ERR_UNSUPPORTED;
-    AIR_CUDA(cudaFuncSetAttribute(rs4_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, AIR_SMEM_OPTIN));
-    rs4_warp_kernel<<<air_counted(1), 32, smem, s>>>(a);
-    AIR_LAUNCH();
-    rs3_finish_kernel<<<air_counted(grid_for(n, 256)), 256, 0, s>>>(n, lam, cf);
-    AIR_LAUNCH();
-    cudaFreeAsync(bits, s);
-    cudaFreeAsync(lam, s);
-    cudaFreeAsync(lines, s);
-    cudaFreeAsync(ovf, s);
-    cudaFreeAsync(ovf_ptr, s);
-    cudaFreeAsync(ocnt, s);
-    cudaFreeAsync(cnt, s);
-    return AIR_OK;
-}
-
 static int rs_first_pass_v3(int64_t n, const int64_t *srp, const int32_t *sci, const int64_t *strp,
                             const int32_t *stci, int32_t max_st, int8_t *cf, int *d_err, cudaStream_t s) {
     RS3Args a;
@@ -1440,8 +1098,6 @@ int air_rs_first_pass(int64_t n, const int64_t *srp, const int32_t *sci, const i
         if (r != AIR_ERR_UNSUPPORTED) return r;
         cached = 2;
     }
-    if (cached == 3 && 2 * max_st + 1 <= 125)
-        return rs_first_pass_v4(n, srp, sci, strp, stci, max_st, max_s, cf, d_err, stats, s);
     if (cached >= 2 && 2 * max_st + 1 <= 125)
         return rs_first_pass_v3(n, srp, sci, strp, stci, max_st, cf, d_err, s);
     RSArgs a;
