@@ -128,6 +128,37 @@ def rotating_pulse(n: int, p: int, nu: float, A: float = 0.1) -> Problem:
                    spec=("rotating_pulse", dict(n=n, p=p, nu=nu, A=A)))
 
 
+def mapped_noisy(n: int = 40, p: int = 2, nu: float = 1e-4, seed: int = 4) -> Problem:
+    """Time-dependent mapped domain with a noisy piecewise-constant velocity.
+
+    The uniform mesh of [0,1]^3 (t, x, y) is deformed by
+    x' = x + 0.05 sin(2 pi t) sin(pi x) sin(pi y), y' likewise (the same
+    displacement); the boundary of the space-time cube stays in place.  Each
+    element e gets the constant velocity (1, 0.5) + 0.1 N(0, 1) (two draws per
+    element, in element order, from numpy.random.default_rng(seed)).  Initial
+    and inflow data are u = sin(pi x) sin(pi y) cos(2 pi t); the source is the
+    one that makes u exact for the mean velocity (1, 0.5), so u solves the
+    problem only approximately.
+    """
+    from .mesh import build_mesh
+    base = manufactured_2d(n=n, p=p, nu=nu, velocity="constant", a_const=(1.0, 0.5))
+
+    def vmap(V):
+        t, x, y = V[:, 0].copy(), V[:, 1].copy(), V[:, 2].copy()
+        d = 0.05 * np.sin(2 * PI * t) * np.sin(PI * x) * np.sin(PI * y)
+        V[:, 1] = x + d
+        V[:, 2] = y + d
+        return V
+
+    E = build_mesh(3, n, reflect=base.reflect).n_elems
+    rng = np.random.default_rng(seed)
+    ev = np.array([1.0, 0.5]) + 0.1 * rng.standard_normal((E, 2))
+    return Problem(D=3, n=n, p=p, nu=nu, velocity=base.velocity, source=base.source,
+                   g_dirichlet=base.g_dirichlet, u_initial=base.u_initial, exact=None,
+                   reflect=base.reflect, vertex_map=vmap, elem_velocity=ev,
+                   name=f"mapped_noisy_n{n}_p{p}", spec=None)
+
+
 def batched_problems(count: int = 16, n_range=(16, 48), seed: int = 2010_11130):
     """Independent 2D+time problems of uneven size for batched solves.
 

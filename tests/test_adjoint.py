@@ -69,3 +69,40 @@ def test_oracle_solves_the_transposed_system():
     H = oracle.setup(s.row_ptr, s.col, s.val, theta=0.25, max_coarse=100)
     _, it_f, _, ok_f, _ = oracle.gmres(s.row_ptr, s.col, s.val, H, s.rhs, rtol=1e-8)
     assert ok_f and it_t <= 2 * it_f + 5
+
+
+def test_mapped_noisy_recipe():
+    """Time-dependent mapped domain with noisy element velocities: the map
+    keeps the space-time cube's boundary, the velocities are (1, 0.5) plus
+    0.1 N(0,1) from default_rng(4) in element order, and block scaling still
+    gives a unit diagonal."""
+    from sthdg.mesh import build_mesh
+    from sthdg.problems import mapped_noisy
+    pr = mapped_noisy(3, 1, 1e-4)
+    m0 = build_mesh(3, 3, reflect=pr.reflect)
+    m1 = build_mesh(3, 3, reflect=pr.reflect, vertex_map=pr.vertex_map)
+    V0, V1 = m0.verts, m1.verts
+    on_bnd = np.any((V0[:, 1:] == 0.0) | (V0[:, 1:] == 1.0), axis=1) | (V0[:, 0] == 0.0) | (V0[:, 0] == 1.0)
+    assert np.allclose(V1[on_bnd], V0[on_bnd], atol=1e-15)
+    assert np.abs(V1 - V0).max() > 1e-3
+    rng = np.random.default_rng(4)
+    assert np.array_equal(pr.elem_velocity, np.array([1.0, 0.5]) + 0.1 * rng.standard_normal((m0.n_elems, 2)))
+    s = assemble(pr)
+    A = sp.csr_matrix((s.val, s.col, s.row_ptr), shape=(s.n, s.n))
+    assert np.array_equal(A.diagonal(), np.ones(s.n))
+
+
+def test_mapped_noisy_adjoint_matches_central_differences():
+    from sthdg.problems import mapped_noisy
+    s = assemble(mapped_noisy(2, 1, 1e-4))
+    rng = np.random.default_rng(12)
+    A = _dense(s)
+    ut = rng.standard_normal(s.n)
+    u = np.linalg.solve(A, s.rhs)
+    lam = np.linalg.solve(A.T, u - ut)
+    h = 1e-6
+    for k in rng.choice(s.n, 3, replace=False):
+        e = np.zeros(s.n)
+        e[k] = h
+        fd = (_loss(A, s.rhs + e, ut) - _loss(A, s.rhs - e, ut)) / (2 * h)
+        assert abs(fd - lam[k]) <= 1e-6 * max(1.0, abs(lam[k]))

@@ -149,3 +149,39 @@ def test_autograd_gradient_matches_central_differences():
         e[k] = h
         fd = (loss(b0 + e) - loss(b0 - e)) / (2 * h)
         assert abs(fd - g[k]) <= 1e-6 * max(1.0, abs(g[k]))
+
+
+def test_adjoint_on_mapped_noisy_domain_matches_dense_lu():
+    """The time-dependent mapped domain with noisy element velocities (its
+    4^3 copy, dense LU as reference)."""
+    from sthdg.problems import mapped_noisy
+    s = assemble(mapped_noisy(4, 2, 1e-4))
+    rng = np.random.default_rng(17)
+    ut = rng.standard_normal(s.n)
+    A = air.CSR.from_host(s.row_ptr, s.col, s.val)
+    solver = air.AdjointSolver(A, rtol=1e-12)
+    b = torch.from_numpy(s.rhs.copy()).cuda().requires_grad_(True)
+    (0.5 * torch.sum((solver.solve(b) - torch.from_numpy(ut).cuda()) ** 2)).backward()
+    D = _scipy(s).toarray()
+    lam = np.linalg.solve(D.T, np.linalg.solve(D, s.rhs) - ut)
+    assert np.linalg.norm(b.grad.cpu().numpy() - lam) <= 1e-9 * np.linalg.norm(lam)
+
+
+def test_adjoint_on_mapped_noisy_8cubed_central_differences():
+    from sthdg.problems import mapped_noisy
+    s = assemble(mapped_noisy(8, 2, 1e-4))
+    rng = np.random.default_rng(19)
+    ut = torch.from_numpy(rng.standard_normal(s.n)).cuda()
+    A = air.CSR.from_host(s.row_ptr, s.col, s.val)
+    solver = air.AdjointSolver(A, rtol=1e-12)
+    b0 = torch.from_numpy(s.rhs.copy()).cuda()
+    b = b0.clone().requires_grad_(True)
+    (0.5 * torch.sum((solver.solve(b) - ut) ** 2)).backward()
+    g = b.grad.cpu().numpy()
+    h = 1e-4      # L is quadratic in b: central differences are exact up to rounding
+    for k in rng.choice(s.n, 3, replace=False):
+        e = torch.zeros_like(b0)
+        e[k] = h
+        lp = 0.5 * float(torch.sum((solver.solve(b0 + e) - ut) ** 2))
+        lm = 0.5 * float(torch.sum((solver.solve(b0 - e) - ut) ** 2))
+        assert abs((lp - lm) / (2 * h) - g[k]) <= 1e-6 * max(1.0, abs(g[k]))
