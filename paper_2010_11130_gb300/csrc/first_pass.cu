@@ -294,6 +294,11 @@ __global__ void __launch_bounds__(32) rs5_warp_kernel(RS5Args a) {
     int64_t steps = 0;
     unsigned long long picks = 0, refills = 0, visits = 0, longs = 0, moves = 0;
     bool failed = false;
+    // the block of the predicted next pick (the next member of the current
+    // cursor line), loaded while the current pick settles
+    int32_t pi = -1;
+    uint32_t pe0 = 0u, pe1 = 0u;
+    uint64_t pm0 = 0ull, pm1 = 0ull;
     while (true) {
         // ---- the pick: lowest member of the highest non-empty bucket
         while (top >= 1 && s.pop[top] == 0) --top;
@@ -328,19 +333,42 @@ __global__ void __launch_bounds__(32) rs5_warp_kernel(RS5Args a) {
         const int32_t i = lbase + sw * 32 + (__ffs(word) - 1);
         if (++picks > (unsigned long long)a.n || i >= a.n) { failed = true; break; }
         // the next members of the same line are the likely next picks: warm their blocks in L2
+        int32_t nxt = -1;
         {
             const uint32_t rest = lane == sw ? (word & (word - 1u)) : wv;
             const unsigned nz = __ballot_sync(FULL, rest != 0u);
             if (rest != 0u && __popc(nz & lanemask_lt()) < 3)
                 prefetch_block(a.blocks + (size_t)(lbase + lane * 32 + (__ffs(rest) - 1)) * BLK_W);
+            if (nz) {
+                const int fl = __ffs(nz) - 1;
+                const uint32_t rw = __shfl_sync(FULL, rest, fl);
+                nxt = lbase + fl * 32 + (__ffs(rw) - 1);
+            }
         }
 
-        // ---- round trip 1: the neighbourhood of i (positions lane and lane + 32)
-        const uint32_t *blk = a.blocks + (size_t)i * BLK_W;
-        const uint64_t *bmk = (const uint64_t *)(blk + BLK_E);
-        const uint32_t e0 = __ldcg(blk + lane), e1 = __ldcg(blk + 32 + lane);
-        const uint64_t m0 = __ldcg((const unsigned long long *)bmk + lane);
-        const uint64_t m1 = __ldcg((const unsigned long long *)bmk + 32 + lane);
+        // ---- round trip 1: the neighbourhood of i (positions lane and lane + 32),
+        // already in registers when i was the predicted pick
+        uint32_t e0, e1;
+        uint64_t m0, m1;
+        if (i == pi) {
+            e0 = pe0; e1 = pe1; m0 = pm0; m1 = pm1;
+        } else {
+            const uint32_t *blk = a.blocks + (size_t)i * BLK_W;
+            const uint64_t *bmk = (const uint64_t *)(blk + BLK_E);
+            e0 = __ldcg(blk + lane);
+            e1 = __ldcg(blk + 32 + lane);
+            m0 = __ldcg((const unsigned long long *)bmk + lane);
+            m1 = __ldcg((const unsigned long long *)bmk + 32 + lane);
+        }
+        pi = nxt;                                        // start loading the predicted next block
+        if (nxt >= 0) {
+            const uint32_t *nb = a.blocks + (size_t)nxt * BLK_W;
+            const uint64_t *nm = (const uint64_t *)(nb + BLK_E);
+            pe0 = __ldcg(nb + lane);
+            pe1 = __ldcg(nb + 32 + lane);
+            pm0 = __ldcg((const unsigned long long *)nm + lane);
+            pm1 = __ldcg((const unsigned long long *)nm + 32 + lane);
+        }
         const uint32_t hdr = __shfl_sync(FULL, e0, 0);
         const int np = (int)(hdr & 2047u) + 1;           // positions: header + entries
         const int nj = (int)((hdr >> 11) & 63u);         // entries 0 .. nj-1 are S^T_i (positions 1 .. nj)
