@@ -31,3 +31,20 @@ def test_status_strings_and_defaults():
     assert "iteration cap" in air.status_string(-6)
     o = air.default_options()
     assert abs(o.theta - 0.25) < 1e-15 and o.relax == b"FCF" and o.restart == 30
+
+
+def test_entry_points_reject_missing_arguments_without_a_gpu():
+    """Argument checks come before any CUDA call: NULL or out-of-range
+    arguments return AIR_ERR_INVALID_ARG (-1) on a machine without a GPU."""
+    import ctypes as C
+    air.build()
+    L = air.lib()
+    null = C.c_void_p(0)
+    assert L.air_setup_batch(-1, None, 0.25, 1, None, None, None, None) == -1
+    assert L.air_gmres_solve_batch(-1, None, None, None, None, 1e-8, None, None, None) == -1
+    assert L.air_vcycle_multi(null, 4, null, null, null) == -1
+    assert L.air_vcycle_multi_f32(null, 4, null, null, null) == -1
+    assert L.air_bicgstab_solve_multi(None, null, 4, null, null, 1e-8, null, None) == -1
+    assert L.air_bicgstab_solve(None, null, null, null, 1e-8, null, None) == -1
+    assert L.air_csr_transpose(None, null, null, null, null) == -1
+    assert L.air_csr_outer(None, null, null, 1.0, null, null) == -1
