@@ -220,8 +220,11 @@ int air_gmres_solve(const air_csr *A, const air_hierarchy *H, const double *b, d
  * (2 restart + 1) n + O(restart^2) doubles, so with restart 30 n can reach
  * about 68,000; larger problems return AIR_ERR_NOALLOC_LIMIT before any work.
  * A, b and x must be on the device (A->on_device = 1).  The first call on a
- * device looks up that array's device address (cudaGetSymbolAddress); make
- * it before any stream capture.  All calls share the array and it keeps the
+ * device looks up that array's device address (cudaGetSymbolAddress) and
+ * keeps it for the life of the process; make that first call before any
+ * stream capture, and do not call this function again after a
+ * cudaDeviceReset of that device (the reset reloads the module, and the kept
+ * address would no longer be the array's).  All calls share the array and it keeps the
  * previous call's contents (the solve clears what must start at zero):
  * calls that overlap on the GPU -- from two streams or two host threads --
  * race on it.  Synchronises the stream once per inner step. */

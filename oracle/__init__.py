@@ -93,10 +93,10 @@ class Level:
 class Hierarchy:
     """Oracle AIR hierarchy; owns the C object."""
 
-    def __init__(self, handle, lib):
+    def __init__(self, handle, lib, copy_levels=True):
         self._h, self._lib = handle, lib
         self.levels = []
-        for l in range(lib.ora_nlevels(handle)):
+        for l in range(lib.ora_nlevels(handle) if copy_levels else 0):
             info = np.zeros(8, dtype=np.int64)
             lib.ora_level_info(handle, l, info)
             n, nnz, snnz, nc, rnnz, nsing, maxm = (int(t) for t in info[:7])
@@ -111,6 +111,15 @@ class Hierarchy:
                 L.pcol = self._get(l, 10, n, np.int32)
                 L.pw = self._get(l, 11, n, np.float64)
             self.levels.append(L)
+
+    def sizes(self):
+        """(rows, stored entries) of every level, without copying the arrays."""
+        out = []
+        for l in range(self._lib.ora_nlevels(self._h)):
+            info = np.zeros(8, dtype=np.int64)
+            self._lib.ora_level_info(self._h, l, info)
+            out.append((int(info[0]), int(info[1])))
+        return out
 
     def _get(self, l, what, count, dtype):
         out = np.empty(count, dtype=dtype)
@@ -136,11 +145,13 @@ class OracleError(RuntimeError):
 
 
 def setup(row_ptr, col, val, theta=0.25, distance=1, max_coarse=1000, max_levels=25,
-          max_dense=4096, relax="FCF", omega=1.0, theta_r=None) -> Hierarchy:
+          max_dense=4096, relax="FCF", omega=1.0, theta_r=None, copy_levels=True) -> Hierarchy:
     """Build the AIR hierarchy (strength, RS splitting, l-AIR R, one-point P, RAP).
 
     theta is the strength threshold of the C/F splitting and one-point P;
-    theta_r (default: theta) that of the l-AIR neighbourhoods of R."""
+    theta_r (default: theta) that of the l-AIR neighbourhoods of R.  With
+    copy_levels=False the level arrays stay inside the C object (levels is
+    empty; vcycle and gmres still work), which saves the copy on large runs."""
     lib = _load()
     rp, ci, v = _csr(row_ptr, col, val)
     st = C.c_int(0)
@@ -149,7 +160,7 @@ def setup(row_ptr, col, val, theta=0.25, distance=1, max_coarse=1000, max_levels
                       int(max_levels), int(max_dense), relax.encode(), float(omega), C.byref(st))
     if not h:
         raise OracleError(f"oracle setup failed with status {st.value}")
-    H = Hierarchy(h, lib)
+    H = Hierarchy(h, lib, copy_levels)
     if st.value != 0:
         raise OracleError(f"oracle setup failed with status {st.value}")
     return H

@@ -32,7 +32,9 @@ static __device__ __align__(256) double g_noalloc_ws[kWsDoubles];
 std::mutex g_mu;
 double *g_ws_addr[kMaxDevices] = {nullptr};
 
-// Device address of g_noalloc_ws on the current device (looked up once).
+// Device address of g_noalloc_ws on the current device, looked up on the
+// first call on each device and kept: a cudaDeviceReset of that device
+// reloads the module and invalidates it (the header tells callers so).
 int workspace_address(double **out) {
     int dev = 0;
     AIR_CUDA(cudaGetDevice(&dev));

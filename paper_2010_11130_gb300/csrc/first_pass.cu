@@ -337,12 +337,15 @@ __global__ void __launch_bounds__(32) rs5_warp_kernel(RS5Args a) {
         {
             const uint32_t rest = lane == sw ? (word & (word - 1u)) : wv;
             const unsigned nz = __ballot_sync(FULL, rest != 0u);
-            if (rest != 0u && __popc(nz & lanemask_lt()) < 3)
-                prefetch_block(a.blocks + (size_t)(lbase + lane * 32 + (__ffs(rest) - 1)) * BLK_W);
+            if (rest != 0u && __popc(nz & lanemask_lt()) < 3) {
+                const int32_t q = lbase + lane * 32 + (__ffs(rest) - 1);
+                if (q < a.n) prefetch_block(a.blocks + (size_t)q * BLK_W);
+            }
             if (nz) {
                 const int fl = __ffs(nz) - 1;
                 const uint32_t rw = __shfl_sync(FULL, rest, fl);
                 nxt = lbase + fl * 32 + (__ffs(rw) - 1);
+                if (nxt >= a.n) nxt = -1;                // a stray bit past the last point: no speculative load
             }
         }
 
