@@ -231,6 +231,113 @@ int air_gmres_solve(const air_csr *A, const air_hierarchy *H, const double *b, d
 int air_gmres_solve_noalloc(const air_csr *A, const air_hierarchy *H, const double *b, double *x,
                             double rtol, void *stream, air_solve_info *info);
 
+/* ------------------------------------------------ HDG assembly on the GPU
+ * The space-time HDG discretisation of advection-diffusion (Section 2.3,
+ * eqs. st-hdg and bilin with the upwind flux sigma_a and the interior-penalty
+ * flux sigma_d of eq. IPpenalty, alpha = 10 p^2 in Section 4), its static
+ * condensation S = D - C A^{-1} B, H = G - C A^{-1} F (Section 2.5,
+ * eqs. linsys and systemLambda) and the left scaling by the facet
+ * block-diagonal inverse (Section 4 settings), assembled on the device into
+ * the CSR trace system that air_setup / air_gmres_solve take.
+ *
+ * Mesh: simplices of a D-dimensional space-time domain (D = 2 for 1D+time,
+ * 3 for 2D+time); coordinates ordered (t, x[, y]).  Facet k of an element is
+ * the one opposite its local vertex k.  Every facet is interior (two
+ * elements), Dirichlet (spatial boundary: its trace is the L2 projection of
+ * the Dirichlet data and is not an unknown) or Neumann (the t = t0 and t = T
+ * faces).  Facet basis: Lagrange on the equispaced lattice of the facet's
+ * canonical frame (its global vertex ids ascending); unknown m of free facet
+ * r is row r b + m, free facets numbered in ascending facet id.  Within a row
+ * the columns ascend; the scaled diagonal block is stored as its b ones.
+ *
+ * All arrays in these three structures are device pointers owned by the
+ * caller.  The reference tables (quadrature, bases on the reference element
+ * and the canonical facet frames; see paper_2010_11130_gb300/hdg_ref.py for
+ * their definitions) are per (D, p) and independent of the mesh. */
+typedef struct {
+    int D;                        /* 2 or 3 */
+    int64_t n_verts, n_elems, n_facets;
+    const double *verts;          /* n_verts x D coordinates */
+    const int32_t *elems;         /* n_elems x (D+1) vertex ids */
+    const int32_t *elem_facets;   /* n_elems x (D+1) facet opposite local vertex k */
+    const int32_t *facets;        /* n_facets x D vertex ids, ascending */
+    const int32_t *facet_elems;   /* n_facets x 2 adjacent elements, ascending, -1 if none */
+    const int8_t *facet_kind;     /* 0 interior, 1 Dirichlet, 2 Neumann */
+} air_hdg_mesh;
+
+typedef struct {
+    int p;                        /* 1, 2 or 3 */
+    int nb, b, nq, nqf, nperm;    /* element / facet basis sizes, volume / facet points, D! */
+    const double *wq;             /* nq volume weights (sum 1/D!) */
+    const double *xq;             /* nq x D volume points */
+    const double *phi, *gphi;     /* nq x nb element basis, nq x nb x D its reference gradient */
+    const double *wf;             /* nqf facet weights (sum 1/(D-1)!) */
+    const double *sq;             /* nqf x (D-1) facet points, canonical frame */
+    const double *psi;            /* nqf x b trace basis */
+    const double *xi_f;           /* (D+1) x nperm x nqf x D facet points in element coordinates */
+    const double *phi_f, *gphi_f; /* (D+1) x nperm x nqf x nb [x D] element basis there */
+    const int32_t *perms;         /* nperm x D: canonical vertex m = local facet vertex perms[s][m] */
+    const double *dir_proj;       /* b x nqf: L2 projection of point values onto the trace basis */
+} air_hdg_ref;
+
+typedef struct {
+    double nu;                    /* diffusion coefficient */
+    double alpha;                 /* interior-penalty parameter (Section 4: 10 p^2) */
+    const double *vel_vol;        /* n_elems x nq x (D-1): spatial velocity at the volume points */
+    const double *src;            /* n_elems x nq: source f at the volume points */
+    const double *vel_face;       /* n_elems x (D+1) x nqf x (D-1): velocity at the facet points */
+    const double *u0_face;        /* n_elems x (D+1) x nqf: data u on Neumann facets; the inflow flux
+                                     g = -a_hat_n u where a_hat_n < 0 (NULL: zero) */
+    const double *g_dir;          /* n_facets x nqf: Dirichlet data at the canonical facet points
+                                     (read on Dirichlet facets only; NULL: zero) */
+} air_hdg_data;
+
+/* Physical coordinates of the quadrature points, for evaluating the data of
+ * air_hdg_data: x_vol n_elems x nq x D, x_face n_elems x (D+1) x nqf x D (the
+ * facet points as each element sees them, in the order of vel_face and
+ * u0_face), x_facet n_facets x nqf x D (canonical facet points, the order of
+ * g_dir).  Any output may be NULL.  Asynchronous on the stream. */
+int air_hdg_points(const air_hdg_mesh *M, const air_hdg_ref *R, double *x_vol, double *x_face, double *x_facet,
+                   void *stream);
+
+/* Rows (= free facets x b) and stored entries of the assembled trace system
+ * (scale = 1: diagonal blocks stored as b ones; 0: full diagonal blocks).
+ * Synchronises the stream.  Errors: INVALID_ARG (D, p or the table sizes). */
+int air_hdg_size(const air_hdg_mesh *M, const air_hdg_ref *R, int scale, int64_t *n_rows, int64_t *nnz,
+                 void *stream);
+
+/* Assemble, condense and (scale = 1) block-scale: row_ptr (n_rows + 1),
+ * col (nnz), val (nnz) and rhs (n_rows), caller-allocated device arrays sized
+ * by air_hdg_size.  diag (optional, n_rows x b) receives the unscaled
+ * diagonal block of every free facet row-major (the D_b of A = D_b^{-1} S),
+ * lam_dir (optional, n_facets x b) the Dirichlet trace values.  One warp per
+ * element builds the local matrices by quadrature, condenses them in shared
+ * memory and writes its off-diagonal blocks; one warp per facet sums the two
+ * diagonal contributions, inverts and scales its row.  Synchronises the
+ * stream.  Errors: INVALID_ARG, CUDA, SINGULAR_COARSE (a singular element
+ * matrix A_K or diagonal block). */
+int air_hdg_assemble(const air_hdg_mesh *M, const air_hdg_ref *R, const air_hdg_data *data, int scale,
+                     int64_t *row_ptr, int32_t *col, double *val, double *rhs, double *diag, double *lam_dir,
+                     void *stream);
+
+/* Gradient of a loss L(Lambda) with respect to a velocity perturbation that
+ * is constant on each element (the element velocities of a piecewise-constant
+ * field).  The trace system S Lambda = H (unscaled) depends on the velocity
+ * through the element matrices; with mu = S^{-T} dL/dLambda,
+ *   dL/da_e = sum over the element's facets and volume of
+ *             mu_K^T (dH_K/da_e - dS_K/da_e Lambda_K),
+ * evaluated without forming dS_K as -(dB_h/da_e)((U, Lambda), (-y, mu)):
+ * U = A_K^{-1}(F_K - B_K Lambda_K) is the element solution and
+ * y = A_K^{-T} C_K^T mu_K.  lam (n_rows) is the solution of the scaled system
+ * A x = b of air_hdg_assemble (the trace unknowns), adj (n_rows) the adjoint
+ * solution of A^T adj = dL/dLambda; mu = D_b^{-T} adj is formed here from
+ * diag (air_hdg_assemble's output) and lam_dir gives Lambda on Dirichlet
+ * facets.  grad (n_elems x (D-1), device) is overwritten.  The source is
+ * taken as independent of the velocity.  Synchronises the stream. */
+int air_hdg_velocity_gradient(const air_hdg_mesh *M, const air_hdg_ref *R, const air_hdg_data *data,
+                              const double *diag, const double *lam_dir, const double *lam, const double *adj,
+                              double *grad, void *stream);
+
 /* Device time of air_setup's phases in milliseconds, summed over levels:
  * ms[0] strength, [1] transpose, [2] C/F splitting, [3] l-AIR restriction,
  * [4] one-point P, [5] Galerkin RAP, [6] coarsest inverse, [7] diagonals,

@@ -44,8 +44,13 @@
  *    more than 0.9 n points (or none), or at max_levels; the coarsest level
  *    is solved by dense LU with partial pivoting.
  *  - V-cycle: zero initial guess on every level, restrict, recurse,
- *    interpolate, then Jacobi sweeps (omega) over the point sets of the
- *    relaxation string ("FCF" = F, C, F; the paper uses Gauss-Seidel).
+ *    interpolate, then the sweeps of the relaxation string, one per
+ *    character: 'F', 'C', 'A' = a Jacobi sweep (weight omega) over the F, C
+ *    or all points ("FCF" = F, C, F); 'f', 'c', 'a' = a forward Gauss-Seidel
+ *    sweep (weight omega, ascending index, each point using the values
+ *    already updated) over the F, C or all points.  "fa" is the paper's
+ *    post-relaxation: forward Gauss-Seidel on the F points, then on all
+ *    points (Section 4 settings).
  *  - GMRES(m): right preconditioned, modified Gram-Schmidt, Givens
  *    rotations, x0 = 0, flexible (stores Z = M^{-1} V), stops when the
  *    true relative residual ||b - A x|| / ||b|| <= rtol (checked at the
@@ -563,11 +568,12 @@ static void coarse_solve(const ora_hier *H, const double *b, double *x) {
     lu_solve_inplace(H->lu, (int)m, x);
 }
 
+/* which: 0 = F points, 1 = C points, 2 = all points; every update from the old x */
 static void jacobi_sweep(const ora_csr *A, const int8_t *cf, int which, double omega,
                          const double *b, double *x, double *tmp) {
     for (int64_t i = 0; i < A->n; ++i) {
         tmp[i] = x[i];
-        if (cf[i] != which) continue;
+        if (which != 2 && cf[i] != which) continue;
         double r = b[i], d = 0.0;
         for (int64_t k = A->rp[i]; k < A->rp[i + 1]; ++k) {
             if (A->ci[k] == i) d = A->v[k];
@@ -576,6 +582,20 @@ static void jacobi_sweep(const ora_csr *A, const int8_t *cf, int which, double o
         tmp[i] = x[i] + omega * r / d;
     }
     memcpy(x, tmp, (size_t)A->n * sizeof(double));
+}
+
+/* which: 0 = F points, 1 = C points, 2 = all points; in place, ascending index */
+static void gauss_seidel_sweep(const ora_csr *A, const int8_t *cf, int which, double omega,
+                               const double *b, double *x) {
+    for (int64_t i = 0; i < A->n; ++i) {
+        if (which != 2 && cf[i] != which) continue;
+        double r = b[i], d = 0.0;
+        for (int64_t k = A->rp[i]; k < A->rp[i + 1]; ++k) {
+            if (A->ci[k] == i) d = A->v[k];
+            r -= A->v[k] * x[A->ci[k]];
+        }
+        x[i] = x[i] + omega * r / d;
+    }
 }
 
 static void vcycle_level(const ora_hier *H, int l, const double *b, double *x) {
@@ -593,8 +613,11 @@ static void vcycle_level(const ora_hier *H, int l, const double *b, double *x) {
     vcycle_level(H, l + 1, bc, xc);
     for (int64_t i = 0; i < n; ++i)                   /* x = P x_c */
         x[i] = L->pcol[i] >= 0 ? L->pw[i] * xc[L->pcol[i]] : 0.0;
-    for (const char *c = H->relax; *c; ++c)
-        jacobi_sweep(&L->A, L->cf, *c == 'C' ? 1 : 0, H->omega, b, x, tmp);
+    for (const char *c = H->relax; *c; ++c) {
+        int which = (*c == 'C' || *c == 'c') ? 1 : (*c == 'A' || *c == 'a') ? 2 : 0;
+        if (*c >= 'a') gauss_seidel_sweep(&L->A, L->cf, which, H->omega, b, x);
+        else jacobi_sweep(&L->A, L->cf, which, H->omega, b, x, tmp);
+    }
     free(bc); free(xc); free(tmp);
 }
 

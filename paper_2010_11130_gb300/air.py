@@ -26,7 +26,8 @@ EXPORTED = ["air_default_options", "air_setup", "air_vcycle", "air_spmv", "air_g
             "air_status_string", "air_kernel_launches", "air_gmres_solve_noalloc", "air_setup_timings",
             "air_csr_transpose", "air_csr_outer", "air_setup_batch", "air_gmres_solve_batch",
             "air_bicgstab_solve", "air_vcycle_multi", "air_bicgstab_solve_multi",
-            "air_vcycle_multi_f32"]
+            "air_vcycle_multi_f32", "air_hdg_points", "air_hdg_size", "air_hdg_assemble",
+            "air_hdg_velocity_gradient"]
 
 
 class air_csr(C.Structure):
@@ -51,6 +52,25 @@ class air_level_info(C.Structure):
     _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("nnz_s", C.c_int64), ("nc", C.c_int64),
                 ("nnz_r", C.c_int64), ("n_singular", C.c_int64), ("max_m", C.c_int32),
                 ("coarsest", C.c_int32)]
+
+
+class air_hdg_mesh(C.Structure):
+    _fields_ = [("D", C.c_int), ("n_verts", C.c_int64), ("n_elems", C.c_int64), ("n_facets", C.c_int64),
+                ("verts", C.c_void_p), ("elems", C.c_void_p), ("elem_facets", C.c_void_p), ("facets", C.c_void_p),
+                ("facet_elems", C.c_void_p), ("facet_kind", C.c_void_p)]
+
+
+class air_hdg_ref(C.Structure):
+    _fields_ = [("p", C.c_int), ("nb", C.c_int), ("b", C.c_int), ("nq", C.c_int), ("nqf", C.c_int),
+                ("nperm", C.c_int), ("wq", C.c_void_p), ("xq", C.c_void_p), ("phi", C.c_void_p),
+                ("gphi", C.c_void_p), ("wf", C.c_void_p), ("sq", C.c_void_p), ("psi", C.c_void_p),
+                ("xi_f", C.c_void_p), ("phi_f", C.c_void_p), ("gphi_f", C.c_void_p), ("perms", C.c_void_p),
+                ("dir_proj", C.c_void_p)]
+
+
+class air_hdg_data(C.Structure):
+    _fields_ = [("nu", C.c_double), ("alpha", C.c_double), ("vel_vol", C.c_void_p), ("src", C.c_void_p),
+                ("vel_face", C.c_void_p), ("u0_face", C.c_void_p), ("g_dir", C.c_void_p)]
 
 
 class AirError(RuntimeError):
@@ -120,6 +140,19 @@ def lib() -> C.CDLL:
                                         C.POINTER(C.c_void_p), C.c_double, C.POINTER(C.c_void_p),
                                         C.POINTER(air_solve_info), C.POINTER(C.c_int)]
     L.air_gmres_solve_batch.restype = C.c_int
+    L.air_hdg_points.argtypes = [C.POINTER(air_hdg_mesh), C.POINTER(air_hdg_ref), C.c_void_p, C.c_void_p,
+                                 C.c_void_p, C.c_void_p]
+    L.air_hdg_points.restype = C.c_int
+    L.air_hdg_size.argtypes = [C.POINTER(air_hdg_mesh), C.POINTER(air_hdg_ref), C.c_int, C.POINTER(C.c_int64),
+                               C.POINTER(C.c_int64), C.c_void_p]
+    L.air_hdg_size.restype = C.c_int
+    L.air_hdg_assemble.argtypes = [C.POINTER(air_hdg_mesh), C.POINTER(air_hdg_ref), C.POINTER(air_hdg_data), C.c_int,
+                                   C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                   C.c_void_p]
+    L.air_hdg_assemble.restype = C.c_int
+    L.air_hdg_velocity_gradient.argtypes = [C.POINTER(air_hdg_mesh), C.POINTER(air_hdg_ref), C.POINTER(air_hdg_data),
+                                            C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    L.air_hdg_velocity_gradient.restype = C.c_int
     _lib = L
     return L
 

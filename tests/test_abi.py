@@ -48,3 +48,23 @@ def test_entry_points_reject_missing_arguments_without_a_gpu():
     assert L.air_bicgstab_solve(None, null, null, null, 1e-8, null, None) == -1
     assert L.air_csr_transpose(None, null, null, null, null) == -1
     assert L.air_csr_outer(None, null, null, 1.0, null, null) == -1
+
+
+def test_hdg_entry_points_reject_missing_arguments_without_a_gpu():
+    import ctypes as C
+    air.build()
+    L = air.lib()
+    null = C.c_void_p(0)
+    n, nnz = C.c_int64(0), C.c_int64(0)
+    assert L.air_hdg_points(None, None, null, null, null, null) == -1
+    assert L.air_hdg_size(None, None, 1, C.byref(n), C.byref(nnz), null) == -1
+    assert L.air_hdg_assemble(None, None, None, 1, null, null, null, null, null, null, null) == -1
+    assert L.air_hdg_velocity_gradient(None, None, None, null, null, null, null, null, null) == -1
+    # a mesh of the wrong dimension or tables of the wrong size
+    from paper_2010_11130_gb300.air import air_hdg_mesh, air_hdg_ref
+    m = air_hdg_mesh(4, 1, 1, 1, 1, 1, 1, 1, 1, 1)
+    r = air_hdg_ref(2, 10, 6, 64, 16, 6)
+    assert L.air_hdg_points(C.byref(m), C.byref(r), null, null, null, null) == -1
+    m.D = 3
+    r.nq = 63
+    assert L.air_hdg_size(C.byref(m), C.byref(r), 1, C.byref(n), C.byref(nnz), null) == -1
