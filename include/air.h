@@ -59,7 +59,7 @@ typedef struct {
 
 typedef struct {
     double theta;        /* classical strength threshold (Section 4: 0.3 for R, 0.2 for C/F) */
-    int distance;        /* l-AIR neighbourhood distance (Section 4: 1); GPU supports 1 */
+    int distance;        /* l-AIR neighbourhood distance (Section 4: 1); 1 or 2 on the GPU */
     char relax[16];      /* Jacobi sweep pattern over point sets, e.g. "FCF" */
     double omega;        /* Jacobi weight */
     int max_coarse;      /* stop coarsening at or below this many rows */
@@ -101,7 +101,10 @@ void air_default_options(air_options *opt);
 /* Build the l-AIR hierarchy of A (Section 3; Section 4 solver settings):
  * classical strength of connection, first-pass Ruge-Stueben C/F splitting,
  * restriction R ~ R_ideal = [-A_cf A_ff^{-1}, I] from one dense local solve
- * per C point, one-point interpolation P = [W; I], Galerkin A_c = R A P;
+ * per C point over its distance-1 or distance-2 neighbourhood of strongly
+ * connected F points (at most 2048 points at distance 2, else UNSUPPORTED),
+ * one-point interpolation P = [W; I],
+ * Galerkin A_c = R A P;
  * repeated until max_coarse, then the coarsest operator is inverted densely.
  * theta and distance override the fields of opt (opt may be NULL for the
  * defaults).  If A is on the device and precision is F64, the hierarchy keeps

@@ -61,6 +61,7 @@ int check_err(air_hierarchy *H, cudaStream_t s) {
     if (e & AIR_DEVERR_CSR) return AIR_ERR_CSR_MALFORMED;
     if (e & AIR_DEVERR_RS_CAP) return AIR_ERR_DEVICE_TIMEOUT;
     if (e & AIR_DEVERR_SINGULAR) return AIR_ERR_SINGULAR_COARSE;
+    if (e & AIR_DEVERR_CAP) return AIR_ERR_UNSUPPORTED;
     return AIR_OK;
 }
 
@@ -213,7 +214,9 @@ int coarsen(air_hierarchy *H, int l, cudaStream_t s, int *stop) {
         AIR_TRY(dalloc(&rsci, nnz_sr));
         AIR_TRY(air_strength(L, o.theta_r, rsrp, rsci, nullptr, 1, s));
     }
-    AIR_TRY(air_lair_counts(nc, L.crows, rsrp ? rsrp : L.srp, rsrp ? rsci : L.sci, L.cf, cnt, s));
+    AIR_TRY(air_lair_counts(nc, L.crows, rsrp ? rsrp : L.srp, rsrp ? rsci : L.sci, L.cf, cnt, o.distance, H->d_err,
+                            s));
+    if (o.distance >= 2) AIR_TRY(check_err(H, s));
     AIR_TRY(dalloc(&L.rrp, nc + 1));
     AIR_TRY(air_exclusive_scan_i32(cnt, L.rrp, nc, s));
     AIR_CUDA(cudaMemsetAsync(dmax, 0, sizeof(int32_t), s));
@@ -232,7 +235,7 @@ int coarsen(air_hierarchy *H, int l, cudaStream_t s, int *stop) {
         LS.srp = rsrp;
         LS.sci = rsci;
     }
-    AIR_TRY(air_lair_solve(LS, L.max_m, dsing, s));
+    AIR_TRY(air_lair_solve(LS, L.max_m, o.distance, dsing, s));
     AIR_TRY(read_i64(dsing, &L.n_singular, s));
     dfree(dsing);
     dfree(rsrp);
@@ -243,9 +246,11 @@ int coarsen(air_hierarchy *H, int l, cudaStream_t s, int *stop) {
     AIR_TRY(air_onepoint_P(L, o.theta, s));
     // a6 Galerkin product
     T.start(5);
-    AIR_TRY(air_rap_terms(L, cnt, s));
+    int32_t *terms = nullptr;
+    AIR_TRY(dalloc(&terms, nc));
+    AIR_TRY(air_rap_terms(L, terms, s));
     AIR_CUDA(cudaMemsetAsync(dmax, 0, sizeof(int32_t), s));
-    AIR_TRY(air_reduce_max_i32(cnt, nc, dmax, s));
+    AIR_TRY(air_reduce_max_i32(terms, nc, dmax, s));
     int32_t max_terms = 0;
     AIR_CUDA(cudaMemcpyAsync(&max_terms, dmax, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     AIR_CUDA(cudaStreamSynchronize(s));
@@ -255,13 +260,14 @@ int coarsen(air_hierarchy *H, int l, cudaStream_t s, int *stop) {
     int64_t *acrp = nullptr;
     int32_t *acci = nullptr;
     double *acv = nullptr;
-    AIR_TRY(air_rap(L, nullptr, nullptr, nullptr, cnt, 0, max_terms, s));
+    AIR_TRY(air_rap(L, nullptr, nullptr, nullptr, cnt, 0, max_terms, terms, s));
     AIR_TRY(dalloc(&acrp, nc + 1));
     AIR_TRY(air_exclusive_scan_i32(cnt, acrp, nc, s));
     AIR_TRY(read_i64(acrp + nc, &C.nnz, s));
     AIR_TRY(dalloc(&acci, C.nnz));
     AIR_TRY(dalloc(&acv, C.nnz));
-    AIR_TRY(air_rap(L, acrp, acci, acv, nullptr, 1, max_terms, s));
+    AIR_TRY(air_rap(L, acrp, acci, acv, nullptr, 1, max_terms, terms, s));
+    dfree(terms);
     C.rp = acrp;
     C.ci = acci;
     C.v = acv;
@@ -596,7 +602,8 @@ int air_setup(const air_csr *A, double theta, int distance, const air_options *o
         o.max_dense < 1 || o.restart < 1 || o.restart > 32 || o.max_iter < 0 ||
         (o.precision != AIR_PREC_F64 && o.precision != AIR_PREC_F32 && o.precision != AIR_PREC_BF16))
         return AIR_ERR_INVALID_ARG;
-    if (distance != 1) return AIR_ERR_UNSUPPORTED;
+    if (distance < 1) return AIR_ERR_INVALID_ARG;
+    if (distance > 2) return AIR_ERR_UNSUPPORTED;
     air_hierarchy *H = new (std::nothrow) air_hierarchy();
     if (!H) return AIR_ERR_OOM;
     AirCallStream call((cudaStream_t)stream);

@@ -67,6 +67,7 @@ void air_dfree(void *p);
 #define AIR_DEVERR_RS_CAP 1
 #define AIR_DEVERR_CSR 2
 #define AIR_DEVERR_SINGULAR 4
+#define AIR_DEVERR_CAP 8        // a fixed per-warp buffer was too small (reported as UNSUPPORTED)
 
 // SELL-32 storage of a set of CSR rows: slice s holds rows 32s .. 32s+31 of
 // the set (in the order of `rows`); entry k of the slice's lane l sits at
@@ -187,12 +188,16 @@ int air_rs_first_pass_cursor(int64_t n, const int64_t *srp, const int32_t *sci, 
                              unsigned long long *stats, cudaStream_t s);
 int air_coarse_ids(int64_t n, const int8_t *cf, int32_t *cid, int32_t *crows, int64_t *work, int64_t *nc,
                    cudaStream_t s);
+// distance 1: N_i = S_i intersect F; distance 2 adds S_k intersect F for k in it
+// (at most 2048 distinct points per C point: more sets AIR_DEVERR_CAP in d_err)
 int air_lair_counts(int64_t nc, const int32_t *crows, const int64_t *srp, const int32_t *sci, const int8_t *cf,
-                    int32_t *cnt, cudaStream_t s);
-int air_lair_solve(const AirLevel &L, int32_t max_m, int64_t *d_nsing, cudaStream_t s);
+                    int32_t *cnt, int distance, int *d_err, cudaStream_t s);
+int air_lair_solve(const AirLevel &L, int32_t max_m, int distance, int64_t *d_nsing, cudaStream_t s);
 int air_onepoint_P(const AirLevel &L, double theta, cudaStream_t s);
+// terms: RAP terms per coarse row (air_rap_terms); rows with more than 2048
+// use a global-memory hash table
 int air_rap(const AirLevel &L, int64_t *acrp, int32_t *acci, double *acv, int32_t *cnt, int fill,
-            int32_t max_terms, cudaStream_t s);
+            int32_t max_terms, const int32_t *terms, cudaStream_t s);
 int air_rap_terms(const AirLevel &L, int32_t *terms, cudaStream_t s);
 int air_coarse_inverse(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, double *inv,
                        double *work, int *d_err, cudaStream_t s);

@@ -636,6 +636,100 @@ __global__ void lair_count_kernel(int64_t nc, const int32_t *crows, const int64_
     }
 }
 
+// Distance-two neighbourhood N_i = (S_i intersect F) plus (S_k intersect F)
+// for every k in S_i intersect F, ascending and without repeats, built by one
+// warp in buf (LAIR_CAP ints): the candidates go into an open-addressing hash
+// set in buf (repeats dropped), the distinct points are compacted to the
+// front and sorted by a bitonic network.  Returns m, or -1 when more than
+// LAIR_CAP / 2 distinct points are found.
+constexpr int LAIR_CAP = 4096;
+
+__device__ __forceinline__ bool hash_insert(int32_t *tab, int32_t key) {
+    uint32_t h = ((uint32_t)key * 2654435761u) & (LAIR_CAP - 1);
+    for (int probe = 0; probe < LAIR_CAP; ++probe) {
+        const int32_t old = atomicCAS(&tab[h], -1, key);
+        if (old == -1) return true;         // inserted
+        if (old == key) return false;       // already present
+        h = (h + 1) & (LAIR_CAP - 1);
+    }
+    return false;
+}
+
+__device__ int lair_neighbourhood2(int32_t i, const int64_t *srp, const int32_t *sci, const int8_t *cf,
+                                   int32_t *buf) {
+    const int lane = threadIdx.x & 31;
+    for (int t = lane; t < LAIR_CAP; t += 32) buf[t] = -1;
+    __syncwarp();
+    int m = 0;
+    bool full = false;
+    // distance one, then the F points strongly connected to each of them
+    for (int64_t q0 = srp[i]; q0 < srp[i + 1]; q0 += 32) {
+        const int64_t q = q0 + lane;
+        const int32_t j = q < srp[i + 1] ? sci[q] : -1;
+        const bool ins = j >= 0 && cf[j] == CF_F && !full && hash_insert(buf, j);
+        m += __popc(__ballot_sync(FULL, ins));
+        full = full || m > LAIR_CAP / 2;
+    }
+    __syncwarp();
+    for (int64_t qa = srp[i]; qa < srp[i + 1]; ++qa) {
+        const int32_t k = sci[qa];
+        if (cf[k] != CF_F) continue;
+        for (int64_t q0 = srp[k]; q0 < srp[k + 1]; q0 += 32) {
+            const int64_t q = q0 + lane;
+            const int32_t j = q < srp[k + 1] ? sci[q] : -1;
+            const bool ins = j >= 0 && cf[j] == CF_F && !full && hash_insert(buf, j);
+            m += __popc(__ballot_sync(FULL, ins));
+            full = full || m > LAIR_CAP / 2;
+        }
+    }
+    __syncwarp();
+    if (full) return -1;
+    // compact the occupied slots to the front (writes never pass the chunk being read)
+    int c = 0;
+    for (int t0 = 0; t0 < LAIR_CAP; t0 += 32) {
+        const int32_t v = buf[t0 + lane];
+        __syncwarp();
+        const bool keep = v >= 0;
+        const unsigned bal = __ballot_sync(FULL, keep);
+        if (keep) buf[c + __popc(bal & lanemask_lt())] = v;
+        c += __popc(bal);
+        __syncwarp();
+    }
+    int P = 32;
+    while (P < c) P <<= 1;
+    for (int t = c + lane; t < P; t += 32) buf[t] = INT32_MAX;
+    __syncwarp();
+    for (int k = 2; k <= P; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int t = lane; t < P; t += 32) {
+                const int u = t ^ j;
+                if (u > t) {
+                    const int32_t x = buf[t], y = buf[u];
+                    const bool up = (t & k) == 0;
+                    if ((x > y) == up) { buf[t] = y; buf[u] = x; }
+                }
+            }
+            __syncwarp();
+        }
+    return c;
+}
+
+// Distance two: one warp per C point counts m_i + 1 entries of R row i.
+__global__ void lair_count2_kernel(int64_t nc, const int32_t *crows, const int64_t *srp, const int32_t *sci,
+                                   const int8_t *cf, int32_t *cnt, int *err) {
+    extern __shared__ int32_t cbuf[];
+    int32_t *buf = cbuf + (threadIdx.x >> 5) * LAIR_CAP;
+    const int lane = threadIdx.x & 31;
+    for (int64_t t = global_warp(); t < nc; t += warp_count()) {
+        const int m = lair_neighbourhood2(crows[t], srp, sci, cf, buf);
+        if (lane == 0) {
+            if (m < 0) atomicOr(err, AIR_DEVERR_CAP);
+            cnt[t] = (m < 0 ? 0 : m) + 1;
+        }
+        __syncwarp();
+    }
+}
+
 __device__ __forceinline__ int find_sorted(const int32_t *arr, int m, int32_t key) {
     int lo = 0, hi = m - 1;
     while (lo <= hi) {
@@ -653,11 +747,12 @@ __device__ __forceinline__ int find_sorted(const int32_t *arr, int m, int32_t ke
 // explicitly rounded operations.  |pivot| <= 1e-14 max|M| -> z = 0.
 __global__ void lair_solve_kernel(int64_t nc, const int32_t *crows, const int64_t *rp, const int32_t *ci,
                                   const double *v, const int64_t *srp, const int32_t *sci, const int8_t *cf,
-                                  const int64_t *rrp, int32_t *rci, double *rv, int maxm, int ld,
+                                  const int64_t *rrp, int32_t *rci, double *rv, int maxm, int ld, int distance,
                                   unsigned long long *nsing) {
     extern __shared__ double lsm[];
     int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    int64_t per_warp = (int64_t)maxm * ld + maxm + (maxm + 1) / 2 + 1;   // doubles
+    const int nints = distance >= 2 ? LAIR_CAP : maxm;
+    int64_t per_warp = (int64_t)maxm * ld + maxm + (nints + 1) / 2 + 1;   // doubles
     double *M = lsm + wib * per_warp;
     double *z = M + (int64_t)maxm * ld;
     int32_t *N = (int32_t *)(z + maxm);
@@ -665,13 +760,18 @@ __global__ void lair_solve_kernel(int64_t nc, const int32_t *crows, const int64_
         int32_t i = crows[t];
         // neighbourhood
         int m = 0;
-        for (int64_t q0 = srp[i]; q0 < srp[i + 1]; q0 += 32) {
-            int64_t q = q0 + lane;
-            int32_t j = q < srp[i + 1] ? sci[q] : -1;
-            bool f = j >= 0 && cf[j] == CF_F;
-            unsigned bal = __ballot_sync(FULL, f);
-            if (f) N[m + __popc(bal & lanemask_lt())] = j;
-            m += __popc(bal);
+        if (distance >= 2) {
+            m = lair_neighbourhood2(i, srp, sci, cf, N);
+            if (m < 0 || m > maxm) m = 0;      // cannot happen: the count pass saw the same sets
+        } else {
+            for (int64_t q0 = srp[i]; q0 < srp[i + 1]; q0 += 32) {
+                int64_t q = q0 + lane;
+                int32_t j = q < srp[i + 1] ? sci[q] : -1;
+                bool f = j >= 0 && cf[j] == CF_F;
+                unsigned bal = __ballot_sync(FULL, f);
+                if (f) N[m + __popc(bal & lanemask_lt())] = j;
+                m += __popc(bal);
+            }
         }
         for (int64_t s = lane; s < (int64_t)m * ld; s += 32) M[s] = 0.0;
         for (int s = lane; s < m; s += 32) z[s] = 0.0;
@@ -812,23 +912,29 @@ __global__ void rap_terms_kernel(int64_t nc, const int64_t *rrp, const int32_t *
 }
 
 // One warp per coarse row i.  Stage 1: (RA)_ij over R entries k ascending and
-// A row k, accumulated into a per-warp shared hash table (within one k the
-// columns j are distinct, so no two lanes touch one slot).  Stage 2: keys
-// (P(j), j) sorted by a bitonic network, then every coarse column sums its
-// terms in ascending j.  COUNT mode only counts the coarse columns.
-template <bool FILL>
-__global__ void rap_kernel(int64_t nc, const int64_t *rrp, const int32_t *rci, const double *rv,
-                           const int64_t *rp, const int32_t *ci, const double *v, const int32_t *pcol,
-                           int hs_bits, int32_t *cnt, const int64_t *acrp, int32_t *acci, double *acv) {
+// A row k, accumulated into a per-warp hash table (within one k the columns j
+// are distinct, so no two lanes touch one slot).  Stage 2: keys (P(j), j)
+// sorted by a bitonic network, then every coarse column sums its terms in
+// ascending j.  COUNT mode only counts the coarse columns.  The table lives in
+// shared memory, or (GMEM, for rows with more terms than fit there) in a
+// global scratch area of HS x 20 bytes per warp of the grid.  rows (if not
+// NULL) lists the nrows coarse rows to process.
+template <bool FILL, bool GMEM>
+__global__ void rap_kernel(int64_t nrows, const int32_t *rows, const int64_t *rrp, const int32_t *rci,
+                           const double *rv, const int64_t *rp, const int32_t *ci, const double *v,
+                           const int32_t *pcol, int hs_bits, unsigned char *gscratch, int32_t *cnt,
+                           const int64_t *acrp, int32_t *acci, double *acv) {
     extern __shared__ unsigned char rsm[];
     const int HS = 1 << hs_bits, HH = HS >> 1;
     int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    unsigned char *base = rsm + (size_t)wib * (size_t)HS * 20;
+    unsigned char *base = GMEM ? gscratch + (size_t)global_warp() * (size_t)HS * 20
+                               : rsm + (size_t)wib * (size_t)HS * 20;
     double *vals = (double *)base;                          // HS
     unsigned long long *skey = (unsigned long long *)(vals + HS);   // HH
     double *sval = (double *)(skey + HH);                   // HH
     int32_t *keys = (int32_t *)(sval + HH);                 // HS
-    for (int64_t t = global_warp(); t < nc; t += warp_count()) {
+    for (int64_t u = global_warp(); u < nrows; u += warp_count()) {
+        const int64_t t = rows ? (int64_t)rows[u] : u;
         for (int s = lane; s < HS; s += 32) keys[s] = -1;
         __syncwarp();
         for (int64_t q = rrp[t]; q < rrp[t + 1]; ++q) {
@@ -1178,17 +1284,24 @@ int air_point_list(int64_t n, const int8_t *cf, int which, int32_t *list, int64_
 }
 
 int air_lair_counts(int64_t nc, const int32_t *crows, const int64_t *srp, const int32_t *sci, const int8_t *cf,
-                    int32_t *cnt, cudaStream_t s) {
-    lair_count_kernel<<<air_counted(grid_for(nc, 256)), 256, 0, s>>>(nc, crows, srp, sci, cf, cnt);
+                    int32_t *cnt, int distance, int *d_err, cudaStream_t s) {
+    if (distance >= 2) {
+        const size_t smem = (size_t)8 * LAIR_CAP * sizeof(int32_t);
+        AIR_CUDA(cudaFuncSetAttribute(lair_count2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, AIR_SMEM_OPTIN));
+        lair_count2_kernel<<<air_counted(grid_for(nc * 32, 256)), 256, smem, s>>>(nc, crows, srp, sci, cf, cnt, d_err);
+    } else {
+        lair_count_kernel<<<air_counted(grid_for(nc, 256)), 256, 0, s>>>(nc, crows, srp, sci, cf, cnt);
+    }
     AIR_LAUNCH();
     return AIR_OK;
 }
 
-int air_lair_solve(const AirLevel &L, int32_t max_m, int64_t *d_nsing, cudaStream_t s) {
+int air_lair_solve(const AirLevel &L, int32_t max_m, int distance, int64_t *d_nsing, cudaStream_t s) {
     int maxm = max_m < 1 ? 1 : max_m;
     int ld = maxm | 1;
-    size_t per_warp = ((size_t)maxm * ld + maxm + (maxm + 1) / 2 + 1) * sizeof(double);
-    int warps = (int)((96 * 1024) / per_warp);
+    const int nints = distance >= 2 ? LAIR_CAP : maxm;
+    size_t per_warp = ((size_t)maxm * ld + maxm + (nints + 1) / 2 + 1) * sizeof(double);
+    int warps = (int)(((distance >= 2 ? AIR_SMEM_OPTIN : 96 * 1024)) / per_warp);
     if (warps > 8) warps = 8;
     if (warps < 1) {
         if (per_warp > AIR_SMEM_OPTIN) return AIR_ERR_UNSUPPORTED;
@@ -1200,7 +1313,7 @@ int air_lair_solve(const AirLevel &L, int32_t max_m, int64_t *d_nsing, cudaStrea
     if (blocks > 152 * 16) blocks = 152 * 16;
     if (blocks < 1) blocks = 1;
     lair_solve_kernel<<<air_counted((unsigned)blocks), warps * 32, smem, s>>>(L.nc, L.crows, L.rp, L.ci, L.v, L.srp, L.sci, L.cf,
-                                                                L.rrp, L.rci, L.rv, maxm, ld,
+                                                                L.rrp, L.rci, L.rv, maxm, ld, distance,
                                                                 (unsigned long long *)d_nsing);
     AIR_LAUNCH();
     return AIR_OK;
@@ -1218,30 +1331,76 @@ int air_rap_terms(const AirLevel &L, int32_t *terms, cudaStream_t s) {
     return AIR_OK;
 }
 
+// Rows whose term count exceeds lim go to the long list, the others to the short one.
+__global__ void rap_split_kernel(int64_t nc, const int32_t *terms, int32_t lim, int32_t *shortr, int32_t *longr,
+                                 unsigned long long *counts) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nc; t += (int64_t)gridDim.x * blockDim.x) {
+        if (terms[t] > lim) longr[atomicAdd(&counts[1], 1ull)] = (int32_t)t;
+        else shortr[atomicAdd(&counts[0], 1ull)] = (int32_t)t;
+    }
+}
+
+template <bool FILL>
+int rap_launch(const AirLevel &L, int64_t nrows, const int32_t *rows, int bits, bool gmem, int32_t *cnt,
+               const int64_t *acrp, int32_t *acci, double *acv, cudaStream_t s) {
+    if (nrows <= 0) return AIR_OK;
+    const size_t per_warp = (size_t)(1 << bits) * 20;
+    if (!gmem) {
+        int warps = (int)((160 * 1024) / per_warp);
+        if (warps > 8) warps = 8;
+        if (warps < 1) warps = 1;
+        int64_t blocks = (nrows + warps - 1) / warps;
+        if (blocks > 152 * 16) blocks = 152 * 16;
+        AIR_CUDA(cudaFuncSetAttribute(rap_kernel<FILL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      AIR_SMEM_OPTIN));
+        rap_kernel<FILL, false><<<air_counted((unsigned)blocks), warps * 32, per_warp * warps, s>>>(
+            nrows, rows, L.rrp, L.rci, L.rv, L.rp, L.ci, L.v, L.pcol, bits, nullptr, cnt, acrp, acci, acv);
+        AIR_LAUNCH();
+        return AIR_OK;
+    }
+    // one scratch table per warp of a grid of at most 152 x 4 warps (8 per block)
+    int64_t blocks = (nrows + 7) / 8;
+    if (blocks > 152 * 4 / 8) blocks = 152 * 4 / 8;
+    unsigned char *scratch = nullptr;
+    AIR_CUDA(air_dmalloc((void **)&scratch, per_warp * (size_t)blocks * 8));
+    rap_kernel<FILL, true><<<air_counted((unsigned)blocks), 256, 0, s>>>(nrows, rows, L.rrp, L.rci, L.rv, L.rp, L.ci,
+                                                                        L.v, L.pcol, bits, scratch, cnt, acrp, acci,
+                                                                        acv);
+    cudaError_t e = cudaGetLastError();
+    air_dfree(scratch);
+    if (e != cudaSuccess) return AIR_ERR_CUDA;
+    return AIR_OK;
+}
+
 int air_rap(const AirLevel &L, int64_t *acrp, int32_t *acci, double *acv, int32_t *cnt, int fill,
-            int32_t max_terms, cudaStream_t s) {
+            int32_t max_terms, const int32_t *terms, cudaStream_t s) {
     int bits = 5;
     while ((1 << bits) < 2 * (max_terms > 1 ? max_terms : 1)) ++bits;
-    size_t per_warp = (size_t)(1 << bits) * 20;
-    if (per_warp > AIR_SMEM_OPTIN) return AIR_ERR_UNSUPPORTED;
-    int warps = (int)((160 * 1024) / per_warp);
-    if (warps > 8) warps = 8;
-    if (warps < 1) warps = 1;
-    size_t smem = per_warp * warps;
-    int64_t blocks = (L.nc + warps - 1) / warps;
-    if (blocks > 152 * 16) blocks = 152 * 16;
-    if (blocks < 1) blocks = 1;
-    if (fill) {
-        AIR_CUDA(cudaFuncSetAttribute(rap_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, AIR_SMEM_OPTIN));
-        rap_kernel<true><<<air_counted((unsigned)blocks), warps * 32, smem, s>>>(L.nc, L.rrp, L.rci, L.rv, L.rp, L.ci, L.v, L.pcol,
-                                                                   bits, nullptr, acrp, acci, acv);
-    } else {
-        AIR_CUDA(cudaFuncSetAttribute(rap_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, AIR_SMEM_OPTIN));
-        rap_kernel<false><<<air_counted((unsigned)blocks), warps * 32, smem, s>>>(L.nc, L.rrp, L.rci, L.rv, L.rp, L.ci, L.v, L.pcol,
-                                                                    bits, cnt, nullptr, nullptr, nullptr);
+    constexpr int kSmemBits = 12;                 // 4096 slots, 80 KB: the largest shared table
+    if (bits <= kSmemBits) {
+        return fill ? rap_launch<true>(L, L.nc, nullptr, bits, false, nullptr, acrp, acci, acv, s)
+                    : rap_launch<false>(L, L.nc, nullptr, bits, false, cnt, nullptr, nullptr, nullptr, s);
     }
-    AIR_LAUNCH();
-    return AIR_OK;
+    // split the rows: up to 2048 terms in shared memory, longer rows in global scratch
+    int32_t *lists = nullptr;
+    unsigned long long *counts = nullptr;
+    AIR_CUDA(air_dmalloc((void **)&lists, (size_t)(2 * L.nc + 2) * sizeof(int32_t)));
+    AIR_CUDA(air_dmalloc((void **)&counts, 2 * sizeof(unsigned long long)));
+    AIR_CUDA(cudaMemsetAsync(counts, 0, 2 * sizeof(unsigned long long), s));
+    rap_split_kernel<<<air_counted(grid_for(L.nc, 256)), 256, 0, s>>>(L.nc, terms, 1 << (kSmemBits - 1), lists,
+                                                                      lists + L.nc + 1, counts);
+    unsigned long long hc[2] = {0, 0};
+    AIR_CUDA(cudaMemcpyAsync(hc, counts, sizeof(hc), cudaMemcpyDeviceToHost, s));
+    AIR_CUDA(cudaStreamSynchronize(s));
+    int st = fill ? rap_launch<true>(L, (int64_t)hc[0], lists, kSmemBits, false, nullptr, acrp, acci, acv, s)
+                  : rap_launch<false>(L, (int64_t)hc[0], lists, kSmemBits, false, cnt, nullptr, nullptr, nullptr, s);
+    if (st == AIR_OK)
+        st = fill ? rap_launch<true>(L, (int64_t)hc[1], lists + L.nc + 1, bits, true, nullptr, acrp, acci, acv, s)
+                  : rap_launch<false>(L, (int64_t)hc[1], lists + L.nc + 1, bits, true, cnt, nullptr, nullptr, nullptr,
+                                      s);
+    air_dfree(lists);
+    air_dfree(counts);
+    return st;
 }
 
 // inv: n*n row major.  work: 2*n*n + n + 1 doubles.

@@ -219,8 +219,11 @@ def test_unsupported_and_invalid_options():
     s = _system("st1d_n32_p1")
     A = air.CSR.from_host(s.row_ptr, s.col, s.val)
     with pytest.raises(air.AirError) as e:
-        air.setup(A, distance=2)
+        air.setup(A, distance=3)
     assert e.value.status == -8
+    with pytest.raises(air.AirError) as e:
+        air.setup(A, distance=0)
+    assert e.value.status == -1
     with pytest.raises(air.AirError) as e:
         air.setup(A, relax="FXF")
     assert e.value.status == -1

@@ -189,3 +189,33 @@ def test_lair_singular_count_over_many_blocks():
     Rv = L.R[2].reshape(40, 3)
     assert np.all(Rv[0::2, 1:] == 0.0)               # singular blocks: injection
     assert np.all(Rv[1::2, 1:] != 0.0)               # the others: the local solve
+
+
+# ------------------------------------------------------------ distance-2 l-AIR
+def test_lair_distance2_neighbourhoods_and_invariant():
+    """Distance two (Section 3: l-AIR with larger neighbourhoods): N_i is the
+    strongly connected F points of i and of those F points, recomputed here
+    from the definition; R's columns are N_i plus i and (R A)(i, N_i) = 0."""
+    s = assemble(manufactured_2d(3, 2, 1e-2))
+    H = oracle.setup(s.row_ptr, s.col, s.val, theta=0.25, distance=2, max_coarse=50, max_levels=3)
+    for l, L in enumerate(H.levels[:-1]):
+        Srp, Sci = L.S
+        S = [set(Sci[Srp[i]:Srp[i + 1]].tolist()) for i in range(L.n)]
+        F = set(np.nonzero(L.cf == 0)[0].tolist())
+        A = _sp(*L.A, L.n)
+        Rrp, Rci, Rv = L.R
+        R = sp.csr_matrix((Rv, Rci, Rrp), shape=(L.nc, L.n))
+        RA = (R @ A).tocsr()
+        for r, i in enumerate(np.nonzero(L.cf == 1)[0]):
+            N1 = S[i] & F
+            N = set(N1)
+            for k in N1:
+                N |= S[k] & F
+            cols = Rci[Rrp[r]:Rrp[r + 1]].tolist()
+            assert cols == sorted(N | {int(i)})
+            row = RA.getrow(r).toarray()[0]
+            if N:
+                scale = np.abs(A[sorted(N)][:, sorted(N)]).max()
+                assert np.max(np.abs(row[sorted(N)])) <= 1e-12 * scale * max(1.0, np.abs(Rv[Rrp[r]:Rrp[r + 1]]).max())
+    assert max(L.max_m for L in H.levels[:-1]) > max(
+        oracle.setup(s.row_ptr, s.col, s.val, theta=0.25, distance=1, max_coarse=50, max_levels=3).levels[0].max_m, 0)
