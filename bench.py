@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--p", type=int, default=2)
     ap.add_argument("--nu", type=float, default=1e-6)
     ap.add_argument("--rtol", type=float, default=1e-8)
+    ap.add_argument("--distance", type=int, default=1, help="l-AIR neighbourhood distance (1 or 2)")
+    ap.add_argument("--no-gpu-assembly", action="store_true")
     ap.add_argument("--workers", type=int, default=min(16, os.cpu_count() or 1))
     ap.add_argument("--sample-n", type=int, default=20, help="oracle sample mesh size")
     ap.add_argument("--vcycles", type=int, default=100)
@@ -79,7 +81,7 @@ def workload_config(args):
     return {"workload": f"st2d_hdg_n{n}_p{p}_rotating_nu{args.nu:g}",
             "mesh": f"{n}^3 cubes x 6 tetrahedra", "p": p, "nu": args.nu, "rtol": args.rtol,
             "unknowns": (12 * n ** 3 - 2 * n * n) * (p + 1) * (p + 2) // 2,
-            "theta": 0.25, "distance": 1, "relax": "FCF", "restart": 30,
+            "theta": 0.25, "distance": args.distance, "relax": "FCF", "restart": 30,
             "l2_flush": "inputs larger than L2 (CSR of A is several GB)"}
 
 
@@ -213,6 +215,55 @@ def spmv_bytes(n, nnz):
     return nnz * 12 + (n + 1) * 8 + n * 8 + n * 8
 
 
+# ------------------------------------------------------------ GPU assembly
+def gpu_assembly_leg(args, s, stream):
+    """The same trace system assembled, condensed and block-scaled on the GPU
+    (air_hdg_assemble), timed with CUDA events (median of 3 after a warm-up),
+    and compared with the host-assembled system: pattern identical, values
+    per row relative to the row's largest entry."""
+    import torch
+    from paper_2010_11130_gb300 import hdg
+    from sthdg.mesh import build_mesh
+    from sthdg.problems import manufactured_2d
+    prob = manufactured_2d(n=args.n, p=args.p, nu=args.nu)
+    mesh = build_mesh(prob.D, prob.n, reflect=prob.reflect, lower=prob.lower, upper=prob.upper,
+                      vertex_map=prob.vertex_map)
+    tab = hdg.HdgTables(prob.D, prob.p)
+    hm = hdg.HdgMesh.from_mesh(mesh)
+    xv, xf, xF = hdg.points(hm, tab)
+    xv, xf, xF = xv.cpu().numpy(), xf.cpu().numpy(), xF.cpu().numpy()
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+    data = hdg.HdgData(prob.nu, 10.0 * prob.p ** 2, dev(prob.velocity(xv)), dev(prob.velocity(xf)),
+                       dev(prob.source(xv)), dev(prob.u_initial(xf)), dev(prob.g_dirichlet(xF)))
+    del xv, xf, xF
+    sysg = hdg.assemble(hm, tab, data)
+    del sysg
+    ts = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sysg = hdg.assemble(hm, tab, data)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1) / 1e3)
+        if len(ts) < 3:
+            del sysg
+    same = bool(np.array_equal(sysg.A.col.cpu().numpy(), s.col)) and bool(
+        np.array_equal(sysg.A.row_ptr.cpu().numpy(), s.row_ptr))
+    val = sysg.A.val.cpu().numpy()
+    rows = np.repeat(np.arange(s.n), np.diff(s.row_ptr))
+    scale = np.zeros(s.n)
+    np.maximum.at(scale, rows, np.abs(s.val))
+    err = np.zeros(s.n)
+    np.maximum.at(err, rows, np.abs(val - s.val))
+    rhs_err = float(np.max(np.abs(sysg.rhs.cpu().numpy() - s.rhs)) / np.max(np.abs(s.rhs)))
+    return {"s": float(np.median(ts)), "elements": int(mesh.n_elems), "facets": int(mesh.n_facets),
+            "kernels": "hdg_element_kernel<3,p> (one warp per element) + facet_kernel (one warp per facet)",
+            "pattern_identical": same, "max_row_rel_diff": float(np.max(err / np.maximum(scale, 1e-300))),
+            "rhs_rel_diff": rhs_err, "timing": "median of 3 after a warm-up, CUDA events, data resident"}
+
+
 # ------------------------------------------------------------------ oracle
 _SAMPLE = {}
 
@@ -234,6 +285,8 @@ def host_cpu():
 def full_oracle_iters(args):
     """The oracle's GMRES iteration count on the full workload, from the record
     written by tests/golden/oracle_full_config.py (None if there is none)."""
+    if args.distance != 1:
+        return None
     path = os.path.join(ROOT, "tests", "golden", f"oracle_st2d_n{args.n}_p{args.p}_nu{args.nu:g}.json")
     try:
         with open(path) as f:
@@ -262,7 +315,8 @@ def oracle_sample(args):
     s = _SAMPLE[key]
     full_n = workload_config(args)["unknowns"]
     t0 = time.perf_counter()
-    H = oracle.setup(s.row_ptr, s.col, s.val, theta=0.25, distance=1, max_coarse=1000, copy_levels=False)
+    H = oracle.setup(s.row_ptr, s.col, s.val, theta=0.25, distance=args.distance, max_coarse=1000,
+                     copy_levels=False)
     t_setup = time.perf_counter() - t0
     t0 = time.perf_counter()
     _, its, rr, ok, _ = oracle.gmres(s.row_ptr, s.col, s.val, H, s.rhs, rtol=args.rtol)
@@ -296,7 +350,8 @@ class FullOracle(threading.Thread):
             oracle.build()
             s = self.s
             t0 = time.perf_counter()
-            H = oracle.setup(s.row_ptr, s.col, s.val, theta=0.25, distance=1, max_coarse=1000, copy_levels=False)
+            H = oracle.setup(s.row_ptr, s.col, s.val, theta=0.25, distance=self.args.distance, max_coarse=1000,
+                             copy_levels=False)
             t_setup = time.perf_counter() - t0
             t0 = time.perf_counter()
             _, its, rr, ok, _ = oracle.gmres(s.row_ptr, s.col, s.val, H, s.rhs, rtol=self.args.rtol)
@@ -356,7 +411,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
 
     def step(prec):
-        H = air.setup(A, theta=0.25, distance=1, precision=prec)
+        H = air.setup(A, theta=0.25, distance=args.distance, precision=prec)
         x, info = air.gmres_solve(A, H, b, rtol=args.rtol)
         H.free()
         return info
@@ -401,7 +456,7 @@ def run_ours(args):
     for prec, key in ((1, "f32"), (0, "f64"), (2, "bf16")):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        H = air.setup(A, theta=0.25, distance=1, precision=prec)
+        H = air.setup(A, theta=0.25, distance=args.distance, precision=prec)
         t_setup = time.perf_counter() - t0
         xs = torch.empty_like(b)
         torch.cuda.synchronize()
@@ -436,6 +491,12 @@ def run_ours(args):
     t_spmv = median_time(lambda: air.spmv(A, b, y), stream, args.vcycles)
     sb = spmv_bytes(s.n, s.nnz)
 
+    gpu_asm = None
+    if not args.no_gpu_assembly:
+        gpu_asm = gpu_assembly_leg(args, s, stream)
+        gpu_asm["host_s"] = gen_s
+        torch.cuda.empty_cache()
+
     # end to end through the C ABI with pinned host buffers
     e2e = None
     if not args.no_e2e:
@@ -449,7 +510,7 @@ def run_ours(args):
         tt = []
         for _ in range(1):
             t0 = time.perf_counter()
-            Hh = air.setup(Ah, theta=0.25, distance=1, precision=1)
+            Hh = air.setup(Ah, theta=0.25, distance=args.distance, precision=1)
             _, ih = air.gmres_solve(Ah, Hh, b_h, x_h, rtol=args.rtol)
             Hh.free()
             tt.append(time.perf_counter() - t0)
@@ -507,7 +568,7 @@ def run_ours(args):
             "bound": "latency (one dependent chain of picks; no HBM or ALU roofline applies)",
             "time_s": breakdown["f32"]["setup_phase_ms"]["splitting"] / 1e3,
             "share_of_step": breakdown["f32"]["setup_phase_ms"]["splitting"] / 1e3 / (ms32 / 1e3)},
-        "cpu_baseline": cpu, "parity_full_size": parity_full, "e2e": e2e, "clocks": clk,
+        "cpu_baseline": cpu, "parity_full_size": parity_full, "gpu_assembly": gpu_asm, "e2e": e2e, "clocks": clk,
         "gpu_launches": int(launches32),
         "generate_s": gen_s,
     }
