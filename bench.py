@@ -59,8 +59,9 @@ def parse():
     ap.add_argument("--vcycles", type=int, default=100)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="single", choices=["single", "batched", "multirhs", "table2"],
+    ap.add_argument("--workload", default="single", choices=["single", "batched", "multirhs", "table2", "largest"],
                     help="batched: 16 independent uneven problems set up and solved at once")
+    ap.add_argument("--large-n", type=int, default=56, help="largest workload: cubes per direction")
     ap.add_argument("--batch-count", type=int, default=16)
     ap.add_argument("--batch-nmin", type=int, default=16)
     ap.add_argument("--batch-nmax", type=int, default=48)
@@ -729,6 +730,95 @@ def run_table2(args):
                       "data": "synthetic", "rows": rows}))
 
 
+def run_largest(args):
+    """The largest workload: 2D+time on 56^3 cubes x 6 tetrahedra (1,053,696
+    tets), p = 3 (21,011,200 unknowns), boundary-layer velocity
+    a = (1, 0.5 tanh(20 (x - 1/2))), nu = 1e-5, Gaussian initial pulse, zero
+    Dirichlet data.  The trace system is assembled on the GPU (air_hdg_assemble;
+    the host assembly of this size takes tens of minutes); then the FP64, FP32
+    and BF16-off-diagonal hierarchies each precondition FP64 flexible GMRES to
+    1e-10, and one adjoint solve A^T lambda = u (the gradient of 1/2 ||u||^2
+    with respect to the right-hand side) runs on the hierarchy of A^T."""
+    import torch
+    import paper_2010_11130_gb300 as air
+    from paper_2010_11130_gb300 import hdg
+    from sthdg.mesh import build_mesh
+    from sthdg.problems import boundary_layer
+    air.build()
+    stream = torch.cuda.current_stream()
+    prob = boundary_layer(n=args.large_n, p=3, nu=1e-5)
+    t0 = time.perf_counter()
+    mesh = build_mesh(prob.D, prob.n, reflect=prob.reflect)
+    mesh_s = time.perf_counter() - t0
+    tab = hdg.HdgTables(3, 3)
+    hm = hdg.HdgMesh.from_mesh(mesh)
+    t0 = time.perf_counter()
+    xv, xf, xF = hdg.points(hm, tab)
+    xv, xf, xF = xv.cpu().numpy(), xf.cpu().numpy(), xF.cpu().numpy()
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+    data = hdg.HdgData(prob.nu, 10.0 * 9, dev(prob.velocity(xv)), dev(prob.velocity(xf)), None,
+                       dev(prob.u_initial(xf)), dev(prob.g_dirichlet(xF)))
+    del xv, xf, xF
+    data_s = time.perf_counter() - t0
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    asm_ms = []
+    for _ in range(2):
+        torch.cuda.synchronize()
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        sysg = hdg.assemble(hm, tab, data)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        asm_ms.append(e0.elapsed_time(e1))
+    A, b, diag = sysg.A, sysg.rhs, sysg.diag
+    del data
+    torch.cuda.empty_cache()
+    out = {"metric": "AIR-FGMRES time-to-1e-10 (setup+solve s), largest workload, per hierarchy precision",
+           "unit": "s", "n_gpus": 1, "higher_is_better": False, "data": "synthetic",
+           "config": {"workload": f"st2d_hdg_n{args.large_n}_p3_layer_nu1e-05", "mesh": f"{args.large_n}^3 cubes x 6 tetrahedra",
+                      "elements": int(mesh.n_elems), "unknowns": int(A.n), "nnz": int(A.nnz), "rtol": 1e-10,
+                      "theta": 0.25, "distance": 1, "relax": "FCF", "restart": 30},
+           "assembly_gpu_s": [m / 1e3 for m in asm_ms], "mesh_host_s": mesh_s, "data_host_s": data_s}
+    res, xs = {}, {}
+    for prec, key in ((0, "f64"), (1, "f32"), (2, "bf16")):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        H = air.setup(A, theta=0.25, precision=prec)
+        torch.cuda.synchronize()
+        ts = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        x, info = air.gmres_solve(A, H, b, rtol=1e-10)
+        torch.cuda.synchronize()
+        tv = time.perf_counter() - t0
+        res[key] = {"setup_s": ts, "solve_s": tv, "s": ts + tv, "iters": info.iters, "relres": info.relres,
+                    "status": info.status, "levels": H.levels(), "setup_phase_ms": H.setup_timings()}
+        xs[key] = x
+        H.free()
+        torch.cuda.empty_cache()
+    for key in ("f32", "bf16"):
+        res[key]["rel_error_vs_f64"] = float(torch.linalg.norm(xs[key] - xs["f64"]) / torch.linalg.norm(xs["f64"]))
+    del xs["f32"], xs["bf16"]
+    # the adjoint through the block-scaled similar matrix D_b^{-T} A^T D_b^T (identity diagonal
+    # blocks, like A): A^T lam = u  <=>  (D_b^{-T} A^T D_b^T) nu = D_b^{-T} u,  lam = D_b^T nu
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    At = air.transpose_scaled(A, 10, diag)
+    Ht = air.setup(At, theta=0.25, precision=1)
+    torch.cuda.synchronize()
+    ts = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    g = air.block_diag_apply(10, diag, 3, xs["f64"].contiguous())
+    nu_, info = air.gmres_solve(At, Ht, g, rtol=1e-10)
+    lam = air.block_diag_apply(10, diag, 1, nu_)
+    torch.cuda.synchronize()
+    res["adjoint_f32"] = {"form": "D_b^{-T} A^T D_b^T (block-scaled transpose)", "transpose_setup_s": ts,
+                          "solve_s": time.perf_counter() - t0, "iters": info.iters, "relres": info.relres,
+                          "status": info.status}
+    out["results"] = res
+    out["value"] = res["f32"]["s"]
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -739,6 +829,8 @@ def main():
         run_multirhs(args)
     elif args.workload == "table2":
         run_table2(args)
+    elif args.workload == "largest":
+        run_largest(args)
     else:
         run_ours(args)
 

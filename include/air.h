@@ -195,6 +195,29 @@ int air_gmres_solve_batch(int count, const air_csr *A, const air_hierarchy *cons
  * for a host CSR or NULL pointers.  Synchronises the stream once. */
 int air_csr_transpose(const air_csr *A, int64_t *row_ptr_t, int32_t *col_t, double *val_t, void *stream);
 
+/* The adjoint operator in the block-scaled form that l-AIR expects.  A is the
+ * block-scaled system D_b^{-1} S (facet blocks of b unknowns, diag = the n/b
+ * diagonal blocks D_b of S, row-major b x b each, as air_hdg_assemble returns
+ * them).  A^T = S^T D_b^{-T} is scaled on the right, not on the left; the
+ * similar matrix D_b^{-T} A^T D_b^T = D_b^{-T} S^T has identity diagonal
+ * blocks again, like A (Section 4: the left block-diagonal scaling the AIR
+ * solver settings prescribe).  With nu = D_b^{-T} lambda, A^T lambda = g
+ * becomes (D_b^{-T} A^T D_b^T) nu = D_b^{-T} g and lambda = D_b^T nu.
+ *
+ * air_csr_transpose_scaled writes D_b^{-T} A^T D_b^T into caller-owned device
+ * arrays sized like air_csr_transpose's.  Every row of a facet must hold
+ * whole b x b blocks in the same layout with the diagonal block stored as its
+ * b ones (the layout air_hdg_assemble produces); otherwise CSR_MALFORMED.
+ * b <= 11.  Synchronises the stream.
+ *
+ * air_block_diag_apply: y_k = op(D_k) x_k for the nblocks b-blocks of device
+ * vectors x, y (op 0: D, 1: D^T, 2: D^{-1}, 3: D^{-T}); b <= 11.
+ * SINGULAR_COARSE if a block is singular.  Synchronises the stream. */
+int air_csr_transpose_scaled(const air_csr *A, int b, const double *diag, int64_t *row_ptr_t, int32_t *col_t,
+                             double *val_t, void *stream);
+int air_block_diag_apply(int64_t nblocks, int b, const double *diag, int op, const double *x, double *y,
+                         void *stream);
+
 /* out[e] = alpha * u[i] * w[j] for every stored entry e = (i, j) of the device
  * CSR A (the gradient of L over A's values with alpha = -1, u = lambda,
  * w = the forward solution).  out has nnz entries, device, caller-owned; an

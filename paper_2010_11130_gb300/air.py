@@ -27,7 +27,7 @@ EXPORTED = ["air_default_options", "air_setup", "air_vcycle", "air_spmv", "air_g
             "air_csr_transpose", "air_csr_outer", "air_setup_batch", "air_gmres_solve_batch",
             "air_bicgstab_solve", "air_vcycle_multi", "air_bicgstab_solve_multi",
             "air_vcycle_multi_f32", "air_hdg_points", "air_hdg_size", "air_hdg_assemble",
-            "air_hdg_velocity_gradient"]
+            "air_hdg_velocity_gradient", "air_csr_transpose_scaled", "air_block_diag_apply"]
 
 
 class air_csr(C.Structure):
@@ -140,6 +140,11 @@ def lib() -> C.CDLL:
                                         C.POINTER(C.c_void_p), C.c_double, C.POINTER(C.c_void_p),
                                         C.POINTER(air_solve_info), C.POINTER(C.c_int)]
     L.air_gmres_solve_batch.restype = C.c_int
+    L.air_csr_transpose_scaled.argtypes = [C.POINTER(air_csr), C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                           C.c_void_p, C.c_void_p]
+    L.air_csr_transpose_scaled.restype = C.c_int
+    L.air_block_diag_apply.argtypes = [C.c_int64, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
+    L.air_block_diag_apply.restype = C.c_int
     L.air_hdg_points.argtypes = [C.POINTER(air_hdg_mesh), C.POINTER(air_hdg_ref), C.c_void_p, C.c_void_p,
                                  C.c_void_p, C.c_void_p]
     L.air_hdg_points.restype = C.c_int
@@ -372,6 +377,32 @@ def transpose(A: CSR, stream=None) -> CSR:
     return CSR(rp, ci, v, A.n)
 
 
+def transpose_scaled(A: CSR, b: int, diag, stream=None) -> CSR:
+    """air_csr_transpose_scaled: D_b^{-T} A^T D_b^T for the block-scaled A = D_b^{-1} S
+    (diag: the (n/b, b, b) device blocks D_b)."""
+    import torch
+    dev = A.val.device
+    rp = torch.empty(A.n + 1, dtype=torch.int64, device=dev)
+    ci = torch.empty(max(A.nnz, 1), dtype=torch.int32, device=dev)[:A.nnz]
+    v = torch.empty(max(A.nnz, 1), dtype=torch.float64, device=dev)[:A.nnz]
+    Ac = A.c()
+    _check(lib().air_csr_transpose_scaled(C.byref(Ac), int(b), C.c_void_p(diag.data_ptr()), C.c_void_p(rp.data_ptr()),
+                                          C.c_void_p(ci.data_ptr()), C.c_void_p(v.data_ptr()),
+                                          C.c_void_p(_stream(stream))), "air_csr_transpose_scaled")
+    return CSR(rp, ci, v, A.n)
+
+
+def block_diag_apply(b: int, diag, op: int, x, y=None, stream=None):
+    """air_block_diag_apply: y_k = op(D_k) x_k (op 0 D, 1 D^T, 2 D^{-1}, 3 D^{-T})."""
+    import torch
+    if y is None:
+        y = torch.empty_like(x)
+    _check(lib().air_block_diag_apply(int(x.shape[0]) // int(b), int(b), C.c_void_p(diag.data_ptr()), int(op),
+                                      C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()), C.c_void_p(_stream(stream))),
+           "air_block_diag_apply")
+    return y
+
+
 def csr_outer(A: CSR, u, w, alpha: float = 1.0, out=None, stream=None):
     """air_csr_outer: out[e] = alpha * u[i] * w[j] over the stored entries (i, j) of A."""
     import torch
@@ -426,24 +457,33 @@ class AdjointSolver:
     construction time; rebuild the solver after changing them.
     """
 
-    def __init__(self, A: CSR, rtol: float = 1e-8, theta: float = 0.25, **opts):
+    def __init__(self, A: CSR, rtol: float = 1e-8, theta: float = 0.25, block=None, **opts):
+        """block = (b, diag): A is D_b^{-1} S with facet blocks of b unknowns and
+        diag the (n/b, b, b) blocks D_b; the adjoint then solves the block-scaled
+        similar matrix D_b^{-T} A^T D_b^T (identity diagonal blocks, like A)."""
         self.A, self.rtol, self.theta, self.opts = A, rtol, theta, opts
+        self.block = block
         self.H = setup(A, theta=theta, **opts)
         self.At = self.Ht = None
         self.info = self.info_adjoint = None
 
     def adjoint_hierarchy(self):
         if self.Ht is None:
-            self.At = transpose(self.A)
+            self.At = transpose(self.A) if self.block is None else transpose_scaled(self.A, *self.block)
             self.Ht = setup(self.At, theta=self.theta, **self.opts)
         return self.At, self.Ht
 
     def solve_adjoint(self, g):
         At, Ht = self.adjoint_hierarchy()
+        if self.block is not None:
+            b, diag = self.block
+            g = block_diag_apply(b, diag, 3, g)
         lam, info = gmres_solve(At, Ht, g, rtol=self.rtol)
         self.info_adjoint = info
         if info.status != 0:
             raise AirError(info.status, "adjoint solve did not converge")
+        if self.block is not None:
+            lam = block_diag_apply(b, diag, 1, lam)
         return lam
 
     def solve(self, b, val=None):

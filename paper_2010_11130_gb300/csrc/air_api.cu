@@ -691,6 +691,53 @@ int air_csr_transpose(const air_csr *A, int64_t *row_ptr_t, int32_t *col_t, doub
     return st;
 }
 
+int air_csr_transpose_scaled(const air_csr *A, int b, const double *diag, int64_t *row_ptr_t, int32_t *col_t,
+                             double *val_t, void *stream) {
+    if (!A || !diag || !row_ptr_t || !col_t || !val_t || !A->on_device || !A->row_ptr || !A->col || !A->val ||
+        b < 1 || b > 11 || A->n_rows <= 0 || A->n_rows != A->n_cols || A->n_rows % b != 0)
+        return AIR_ERR_INVALID_ARG;
+    AirCallStream call((cudaStream_t)stream);
+    cudaStream_t s = (cudaStream_t)stream;
+    int *d_err = nullptr;
+    AIR_CUDA(cudaMallocAsync(&d_err, sizeof(int), s));
+    AIR_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), s));
+    int st = air_csr_transpose_impl(A->n_rows, A->n_cols, A->nnz, A->row_ptr, A->col, A->val, row_ptr_t, col_t,
+                                    val_t, d_err, s);
+    if (st == AIR_OK) st = air_block_scale_transpose_impl(A->n_rows, b, diag, row_ptr_t, col_t, val_t, d_err, s);
+    int herr = 0;
+    if (st == AIR_OK) {
+        cudaError_t e = cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = AIR_ERR_CUDA;
+    }
+    cudaFreeAsync(d_err, s);
+    if (st == AIR_OK && (herr & AIR_DEVERR_SINGULAR)) st = AIR_ERR_SINGULAR_COARSE;
+    else if (st == AIR_OK && herr) st = AIR_ERR_CSR_MALFORMED;
+    return st;
+}
+
+int air_block_diag_apply(int64_t nblocks, int b, const double *diag, int op, const double *x, double *y,
+                         void *stream) {
+    if (nblocks < 0 || b < 1 || b > 11 || op < 0 || op > 3 || (nblocks > 0 && (!diag || !x || !y)))
+        return AIR_ERR_INVALID_ARG;
+    if (nblocks == 0) return AIR_OK;
+    AirCallStream call((cudaStream_t)stream);
+    cudaStream_t s = (cudaStream_t)stream;
+    int *d_err = nullptr;
+    AIR_CUDA(cudaMallocAsync(&d_err, sizeof(int), s));
+    AIR_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), s));
+    int st = air_block_apply_impl(nblocks, b, diag, op, x, y, d_err, s);
+    int herr = 0;
+    if (st == AIR_OK) {
+        cudaError_t e = cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = AIR_ERR_CUDA;
+    }
+    cudaFreeAsync(d_err, s);
+    if (st == AIR_OK && herr) st = AIR_ERR_SINGULAR_COARSE;
+    return st;
+}
+
 int air_csr_outer(const air_csr *A, const double *u, const double *w, double alpha, double *out, void *stream) {
     if (!A || !A->on_device || A->n_rows < 0 || A->nnz < 0 || !A->row_ptr) return AIR_ERR_INVALID_ARG;
     if (A->nnz > 0 && (!A->col || !u || !w || !out)) return AIR_ERR_INVALID_ARG;

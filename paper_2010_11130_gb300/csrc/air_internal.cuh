@@ -205,6 +205,11 @@ int air_coarse_inverse(int64_t n, const int64_t *rp, const int32_t *ci, const do
 // adjoint.cu
 int air_csr_transpose_impl(int64_t n, int64_t ncols, int64_t nnz, const int64_t *rp, const int32_t *ci,
                            const double *v, int64_t *rpt, int32_t *cit, double *vt, int *d_err, cudaStream_t s);
+// adjoint.cu: A^T with block b x b scaling D_f^{-T} (.) D_g^T, and block-diagonal products
+int air_block_scale_transpose_impl(int64_t n, int b, const double *diag, const int64_t *rpt, const int32_t *cit,
+                                   double *vt, int *d_err, cudaStream_t s);
+int air_block_apply_impl(int64_t nblk, int b, const double *diag, int op, const double *x, double *y, int *d_err,
+                         cudaStream_t s);
 int air_csr_outer_impl(int64_t n, int64_t ncols, const int64_t *rp, const int32_t *ci, const double *u,
                        const double *w, double alpha, double *out, cudaStream_t s);
 

@@ -26,6 +26,7 @@
 #include <math.h>
 
 #include "air_internal.cuh"
+#include "warp_dense.cuh"
 
 namespace {
 
@@ -582,57 +583,6 @@ __global__ void dirichlet_kernel(int64_t F, int B, int NQF, const int8_t *kind, 
             for (int q = 0; q < NQF; ++q) s += proj[m * NQF + q] * gd[f * NQF + q];
         lam[t] = s;
     }
-}
-
-// In-place Gauss-Jordan inversion of the warp's n x n matrix M into Minv
-// (partial pivoting, ties -> smallest row).  W is 2 n^2 scratch.
-__device__ bool warp_inverse(const double *M, int n, double *W, double *Minv) {
-    const int lane = threadIdx.x & 31;
-    const int w2 = 2 * n;
-    for (int t = lane; t < n * w2; t += 32) {
-        const int r = t / w2, c = t % w2;
-        W[t] = c < n ? M[r * n + c] : (c - n == r ? 1.0 : 0.0);
-    }
-    __syncwarp();
-    for (int c = 0; c < n; ++c) {
-        double v = -1.0;
-        int r = n;
-        for (int rr = c + lane; rr < n; rr += 32) {
-            const double av = fabs(W[rr * w2 + c]);
-            if (av > v) { v = av; r = rr; }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const double ov = __shfl_down_sync(FULL, v, o);
-            const int orow = __shfl_down_sync(FULL, r, o);
-            if (ov > v || (ov == v && orow < r)) { v = ov; r = orow; }
-        }
-        r = __shfl_sync(FULL, r, 0);
-        v = __shfl_sync(FULL, v, 0);
-        if (!(v > 0.0)) return false;
-        if (r != c)
-            for (int t = lane; t < w2; t += 32) {
-                const double x = W[c * w2 + t];
-                W[c * w2 + t] = W[r * w2 + t];
-                W[r * w2 + t] = x;
-            }
-        __syncwarp();
-        const double piv = W[c * w2 + c];
-        for (int t = lane; t < w2; t += 32) W[c * w2 + t] = W[c * w2 + t] / piv;
-        __syncwarp();
-        for (int t = lane; t < n * w2; t += 32) {
-            const int rr = t / w2, cc = t % w2;
-            if (rr == c || cc == c) continue;
-            W[t] -= W[rr * w2 + c] * W[c * w2 + cc];
-        }
-        __syncwarp();
-        for (int rr = lane; rr < n; rr += 32)
-            if (rr != c) W[rr * w2 + c] = 0.0;
-        __syncwarp();
-    }
-    for (int t = lane; t < n * n; t += 32) Minv[t] = W[(t / n) * w2 + n + t % n];
-    __syncwarp();
-    return true;
 }
 
 struct FacetArgs {

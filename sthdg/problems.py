@@ -159,6 +159,28 @@ def mapped_noisy(n: int = 40, p: int = 2, nu: float = 1e-4, seed: int = 4) -> Pr
                    name=f"mapped_noisy_n{n}_p{p}", spec=None)
 
 
+def boundary_layer(n: int = 56, p: int = 3, nu: float = 1e-5) -> Problem:
+    """2D+time on [0,1]^3 with a shear layer across x = 1/2 and a Gaussian pulse.
+
+    Velocity a = (1, 0.5 tanh(20 (x - 1/2))), f = 0, zero Dirichlet data on the
+    spatial boundary, initial data u0 = exp(-200 ((x - 0.3)^2 + (y - 0.3)^2))
+    imposed through the inflow flux on t = 0.  No closed-form solution.  The
+    Kuhn diagonal is chosen for the mean velocity (1, 0).
+    """
+    def u0(X):
+        x, y = X[..., 1], X[..., 2]
+        return np.exp(-200.0 * ((x - 0.3) ** 2 + (y - 0.3) ** 2))
+
+    def vel(X):
+        x = X[..., 1]
+        return np.stack([np.ones_like(x), 0.5 * np.tanh(20.0 * (x - 0.5))], axis=-1)
+
+    return Problem(D=3, n=n, p=p, nu=nu, velocity=vel, source=lambda X: np.zeros(X.shape[:-1]),
+                   g_dirichlet=lambda X: np.zeros(X.shape[:-1]), u_initial=u0, exact=None,
+                   reflect=choose_reflection(3, [1.0, 0.0]), name=f"layer_n{n}_p{p}",
+                   spec=("boundary_layer", dict(n=n, p=p, nu=nu)))
+
+
 def batched_problems(count: int = 16, n_range=(16, 48), seed: int = 2010_11130):
     """Independent 2D+time problems of uneven size for batched solves.
 
@@ -184,7 +206,8 @@ def make(spec) -> Problem:
     """Rebuild a problem from its (factory name, kwargs) spec."""
     name, kw = spec
     return {"manufactured_1d": manufactured_1d, "manufactured_2d": manufactured_2d,
-            "pure_advection": pure_advection, "rotating_pulse": rotating_pulse}[name](**kw)
+            "pure_advection": pure_advection, "rotating_pulse": rotating_pulse,
+            "boundary_layer": boundary_layer}[name](**kw)
 
 
 def workload(name: str, **kw) -> Problem:

@@ -68,3 +68,14 @@ def test_hdg_entry_points_reject_missing_arguments_without_a_gpu():
     m.D = 3
     r.nq = 63
     assert L.air_hdg_size(C.byref(m), C.byref(r), 1, C.byref(n), C.byref(nnz), null) == -1
+
+
+def test_adjoint_block_entry_points_reject_bad_arguments_without_a_gpu():
+    import ctypes as C
+    air.build()
+    L = air.lib()
+    null = C.c_void_p(0)
+    assert L.air_csr_transpose_scaled(None, 6, null, null, null, null, null) == -1
+    assert L.air_block_diag_apply(4, 0, null, 0, null, null, null) == -1
+    assert L.air_block_diag_apply(4, 6, null, 7, null, null, null) == -1
+    assert L.air_block_diag_apply(0, 6, null, 0, null, null, null) == 0

@@ -218,3 +218,71 @@ def test_velocity_gradient_8cubed_sampled_central_differences():
             em[e, m] -= h
             fd = (loss(ep) - loss(em)) / (2 * h)
             assert abs(grad[e, m] - fd) <= 1e-4 * np.max(np.abs(grad)) + 1e-9 * L / h, (e, m, grad[e, m], fd)
+
+
+# ------------------------------------------------------ block-scaled adjoint
+def test_transpose_scaled_and_block_apply_match_dense():
+    """D_b^{-T} A^T D_b^T (the adjoint operator with identity diagonal blocks)
+    and the block-diagonal products against dense numpy."""
+    import scipy.sparse as sp
+    from sthdg.problems import boundary_layer
+    prob = boundary_layer(3, 3, 1e-5)
+    mesh = _mesh_of(prob)
+    tab = hdg.HdgTables(3, 3)
+    hm = hdg.HdgMesh.from_mesh(mesh)
+    sys_ = hdg.assemble(hm, tab, _gpu_data(prob, mesh, hm, tab))
+    A = sys_.A
+    b = tab.b
+    At = air.transpose_scaled(A, b, sys_.diag)
+    torch.cuda.synchronize()
+    n = A.n
+    Ad = sp.csr_matrix((A.val.cpu().numpy(), A.col.cpu().numpy(), A.row_ptr.cpu().numpy()), shape=(n, n)).toarray()
+    Dg = sys_.diag.cpu().numpy()
+    Db = np.zeros((n, n))
+    for k in range(n // b):
+        Db[k * b:(k + 1) * b, k * b:(k + 1) * b] = Dg[k]
+    want = np.linalg.inv(Db).T @ Ad.T @ Db.T
+    pat = air.transpose(A)
+    assert np.array_equal(At.col.cpu().numpy(), pat.col.cpu().numpy())
+    in_pattern = sp.csr_matrix((np.ones(pat.nnz), pat.col.cpu().numpy(), pat.row_ptr.cpu().numpy()),
+                               shape=(n, n)).toarray() != 0
+    got = sp.csr_matrix((At.val.cpu().numpy(), At.col.cpu().numpy(), At.row_ptr.cpu().numpy()),
+                        shape=(n, n)).toarray()
+    scale = np.abs(want).max()
+    assert np.max(np.abs(got - want * in_pattern)) <= 1e-11 * scale
+    # what the pattern leaves out is the roundoff-level part of the diagonal blocks
+    assert np.max(np.abs(want[~in_pattern])) <= 1e-11 * scale
+    x = torch.randn(n, dtype=torch.float64, device="cuda")
+    xh = x.cpu().numpy()
+    ops = {0: Db, 1: Db.T, 2: np.linalg.inv(Db), 3: np.linalg.inv(Db).T}
+    for op, M in ops.items():
+        y = air.block_diag_apply(b, sys_.diag, op, x)
+        torch.cuda.synchronize()
+        assert np.allclose(y.cpu().numpy(), M @ xh, rtol=1e-12, atol=1e-12 * np.abs(M @ xh).max())
+
+
+@pytest.mark.parametrize("n", [6, 10])
+def test_block_scaled_adjoint_solve_matches_dense(n):
+    """A^T lambda = g through the block-scaled similar matrix on the
+    boundary-layer problem (p = 3): lambda against the dense solve, and the
+    scaled form needs no more iterations than the plain transpose."""
+    import scipy.sparse as sp
+    from sthdg.problems import boundary_layer
+    prob = boundary_layer(n, 3, 1e-5)
+    mesh = _mesh_of(prob)
+    tab = hdg.HdgTables(3, 3)
+    hm = hdg.HdgMesh.from_mesh(mesh)
+    sys_ = hdg.assemble(hm, tab, _gpu_data(prob, mesh, hm, tab))
+    g = torch.randn(sys_.A.n, dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(3))
+    S1 = air.AdjointSolver(sys_.A, rtol=1e-11, block=(tab.b, sys_.diag), max_coarse=100)
+    lam = S1.solve_adjoint(g)
+    S0 = air.AdjointSolver(sys_.A, rtol=1e-11, max_coarse=100)
+    lam0 = S0.solve_adjoint(g)
+    torch.cuda.synchronize()
+    assert S1.info_adjoint.iters <= S0.info_adjoint.iters + 2
+    if n == 6:
+        A = sp.csr_matrix((sys_.A.val.cpu().numpy(), sys_.A.col.cpu().numpy(), sys_.A.row_ptr.cpu().numpy()),
+                          shape=(sys_.A.n, sys_.A.n)).toarray()
+        ref = np.linalg.solve(A.T, g.cpu().numpy())
+        assert np.linalg.norm(lam.cpu().numpy() - ref) <= 1e-8 * np.linalg.norm(ref)
+    assert np.linalg.norm((lam - lam0).cpu().numpy()) <= 1e-8 * np.linalg.norm(lam0.cpu().numpy())
