@@ -71,6 +71,13 @@ typedef struct {
     int validate;        /* 1: check the CSR before setup (one extra pass) */
     double theta_r;      /* strength threshold of R's l-AIR neighbourhoods; < 0: theta (Section 4
                             uses 0.3 for R with 0.2 for the coarsening) */
+    int falgout_block;   /* 0: C/F splitting by the first pass of Ruge-Stueben over the whole level
+                            (default); a multiple of 1024 up to 8192: Falgout-style splitting
+                            (Section 4 names Falgout coarsening): the first pass runs in every
+                            block of that many consecutive points at once, on the strength graph
+                            restricted to the block, and interface points left F without a strong
+                            C point are fixed by rounds of a parallel independent set (weight
+                            |S^T_i| plus a SplitMix64 fraction of i) */
 } air_options;
 
 typedef struct {
@@ -95,7 +102,7 @@ typedef struct air_hierarchy air_hierarchy;   /* opaque, library-owned */
 
 /* Fill *opt with the defaults: theta 0.25, distance 1, relax "FCF", omega 1,
  * max_coarse 1000, max_levels 25, max_dense 4096, AIR_PREC_F64, restart 30,
- * max_iter 1000, validate 1, theta_r -1 (same as theta). */
+ * max_iter 1000, validate 1, theta_r -1 (same as theta), falgout_block 0. */
 void air_default_options(air_options *opt);
 
 /* Build the l-AIR hierarchy of A (Section 3; Section 4 solver settings):

@@ -42,7 +42,9 @@ def _load():
     lib.ora_spmv.argtypes = [C.c_int64, I64P, I32P, F64P, F64P, F64P]
     lib.ora_spmv.restype = None
     lib.ora_setup.argtypes = [C.c_int64, I64P, I32P, F64P, C.c_double, C.c_double, C.c_int, C.c_int, C.c_int,
-                              C.c_int, C.c_char_p, C.c_double, C.POINTER(C.c_int)]
+                              C.c_int, C.c_char_p, C.c_double, C.c_int64, C.POINTER(C.c_int)]
+    lib.ora_hash_frac.argtypes = [C.c_uint64]
+    lib.ora_hash_frac.restype = C.c_double
     lib.ora_setup.restype = C.c_void_p
     lib.ora_free.argtypes = [C.c_void_p]
     lib.ora_nlevels.argtypes = [C.c_void_p]
@@ -145,19 +147,23 @@ class OracleError(RuntimeError):
 
 
 def setup(row_ptr, col, val, theta=0.25, distance=1, max_coarse=1000, max_levels=25,
-          max_dense=4096, relax="FCF", omega=1.0, theta_r=None, copy_levels=True) -> Hierarchy:
+          max_dense=4096, relax="FCF", omega=1.0, theta_r=None, copy_levels=True,
+          falgout_block=0) -> Hierarchy:
     """Build the AIR hierarchy (strength, RS splitting, l-AIR R, one-point P, RAP).
 
     theta is the strength threshold of the C/F splitting and one-point P;
     theta_r (default: theta) that of the l-AIR neighbourhoods of R.  With
     copy_levels=False the level arrays stay inside the C object (levels is
-    empty; vcycle and gmres still work), which saves the copy on large runs."""
+    empty; vcycle and gmres still work), which saves the copy on large runs.
+    falgout_block > 0 replaces the first pass by the Falgout-style splitting
+    with index blocks of that many points (see air_oracle.c)."""
     lib = _load()
     rp, ci, v = _csr(row_ptr, col, val)
     st = C.c_int(0)
     h = lib.ora_setup(len(rp) - 1, rp, ci, v, float(theta), float(theta if theta_r is None else theta_r),
                       int(distance), int(max_coarse),
-                      int(max_levels), int(max_dense), relax.encode(), float(omega), C.byref(st))
+                      int(max_levels), int(max_dense), relax.encode(), float(omega), int(falgout_block),
+                      C.byref(st))
     if not h:
         raise OracleError(f"oracle setup failed with status {st.value}")
     H = Hierarchy(h, lib, copy_levels)
@@ -197,3 +203,8 @@ def bicgstab(row_ptr, col, val, H, b, rtol=1e-12, max_iter=1000):
                           int(max_iter), C.byref(it), C.byref(rr))
     return x, it.value, rr.value, rc == 0
 
+
+
+def hash_frac(x: int) -> float:
+    """The oracle's SplitMix64 fraction of x (for pins of the Falgout-style splitting)."""
+    return _load().ora_hash_frac(int(x))

@@ -22,6 +22,18 @@
  *    undecided k in S_j of a new F point j gains 1; every undecided k in
  *    S_i loses 1.  Points with S_i and S^T_i both empty start as F; points
  *    still undecided when the largest lambda is 0 become F.
+ *  - Falgout-style splitting (optional, the coarsening of the paper's Section 4
+ *    settings, whose details the paper leaves to its library): the points
+ *    are cut into consecutive index blocks of a fixed size; the first pass
+ *    above runs in each block on the strength graph restricted to the block
+ *    (measures count only dependants inside the block; a point with no strong
+ *    connection inside its block starts F).  Interface points (a strong
+ *    connection, either way, to another block) that end F with S_i non-empty
+ *    but no C point in S_i are then fixed by rounds of a parallel independent
+ *    set: weight w_i = |S^T_i| + frac(i), frac(i) in [0, 1) from the
+ *    SplitMix64 hash of i; a remaining point becomes C when its weight beats
+ *    every remaining point of S_i and S^T_i (ties -> smaller index), and
+ *    points that now have a C point in S_i leave.  One block = the first pass.
  *  - the strength threshold may differ between the C/F splitting (with
  *    one-point P) and the l-AIR neighbourhoods (Section 4 uses 0.2 for the
  *    coarsening and 0.3 for R); R then uses its own strength graph.
@@ -218,14 +230,20 @@ static heap_item heap_pop(heap_t *H) {
 
 #define U_PT 2   /* undecided */
 
-static int rs_first_pass(const ora_csr *S, const ora_csr *ST, int8_t *cf) {
+/* First pass on the points [lo, hi) with the strength graph restricted to
+ * them (the whole graph for lo = 0, hi = n). */
+static int rs_first_pass_range(const ora_csr *S, const ora_csr *ST, int8_t *cf, int64_t lo, int64_t hi) {
     int64_t n = S->n;
     int64_t *lam = (int64_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
     heap_t H = {0};
     if (!lam) return ORA_ERR_OOM;
-    for (int64_t i = 0; i < n; ++i) {
-        lam[i] = ST->rp[i + 1] - ST->rp[i];
-        int isolated = (S->rp[i + 1] == S->rp[i]) && lam[i] == 0;
+#define IN_RANGE(x) ((x) >= lo && (x) < hi)
+    for (int64_t i = lo; i < hi; ++i) {
+        int64_t m = 0, ns = 0;
+        for (int64_t a = ST->rp[i]; a < ST->rp[i + 1]; ++a) m += IN_RANGE(ST->ci[a]);
+        for (int64_t a = S->rp[i]; a < S->rp[i + 1]; ++a) ns += IN_RANGE(S->ci[a]);
+        lam[i] = m;
+        int isolated = ns == 0 && m == 0;
         cf[i] = isolated ? 0 : U_PT;
         if (!isolated && heap_push(&H, (heap_item){lam[i], i})) { free(lam); return ORA_ERR_OOM; }
     }
@@ -237,26 +255,93 @@ static int rs_first_pass(const ora_csr *S, const ora_csr *ST, int8_t *cf) {
         cf[i] = 1;
         for (int64_t a = ST->rp[i]; a < ST->rp[i + 1]; ++a) {
             int64_t j = ST->ci[a];
-            if (cf[j] != U_PT) continue;
+            if (!IN_RANGE(j) || cf[j] != U_PT) continue;
             cf[j] = 0;
             for (int64_t b = S->rp[j]; b < S->rp[j + 1]; ++b) {
                 int64_t k = S->ci[b];
-                if (cf[k] != U_PT) continue;
+                if (!IN_RANGE(k) || cf[k] != U_PT) continue;
                 lam[k] += 1;
                 if (heap_push(&H, (heap_item){lam[k], k})) { free(lam); free(H.h); return ORA_ERR_OOM; }
             }
         }
         for (int64_t a = S->rp[i]; a < S->rp[i + 1]; ++a) {
             int64_t k = S->ci[a];
-            if (cf[k] != U_PT) continue;
+            if (!IN_RANGE(k) || cf[k] != U_PT) continue;
             lam[k] -= 1;
             if (heap_push(&H, (heap_item){lam[k], k})) { free(lam); free(H.h); return ORA_ERR_OOM; }
         }
     }
-    for (int64_t i = 0; i < n; ++i)
+#undef IN_RANGE
+    for (int64_t i = lo; i < hi; ++i)
         if (cf[i] == U_PT) cf[i] = 0;
     free(lam);
     free(H.h);
+    return ORA_OK;
+}
+
+static int rs_first_pass(const ora_csr *S, const ora_csr *ST, int8_t *cf) {
+    return rs_first_pass_range(S, ST, cf, 0, S->n);
+}
+
+/* SplitMix64 (Steele, Lea and Flood, 2014) of x, its top 53 bits as a
+ * fraction in [0, 1). */
+double ora_hash_frac(uint64_t x) {
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z = z ^ (z >> 31);
+    return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+}
+
+static int has_strong_c(const ora_csr *S, const int8_t *cf, int64_t i) {
+    for (int64_t a = S->rp[i]; a < S->rp[i + 1]; ++a)
+        if (cf[S->ci[a]] == 1) return 1;
+    return 0;
+}
+
+/* Falgout-style splitting with blocks of `block` points (see the header). */
+static int falgout_split(const ora_csr *S, const ora_csr *ST, int8_t *cf, int64_t block) {
+    int64_t n = S->n;
+    for (int64_t lo = 0; lo < n; lo += block) {
+        int st = rs_first_pass_range(S, ST, cf, lo, lo + block < n ? lo + block : n);
+        if (st) return st;
+    }
+    int8_t *inU = (int8_t *)calloc((size_t)(n > 0 ? n : 1), 1);
+    int8_t *sel = (int8_t *)calloc((size_t)(n > 0 ? n : 1), 1);
+    if (!inU || !sel) { free(inU); free(sel); return ORA_ERR_OOM; }
+    int64_t nu = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (cf[i] != 0 || S->rp[i + 1] == S->rp[i] || has_strong_c(S, cf, i)) continue;
+        int64_t bi = i / block, cross = 0;
+        for (int64_t a = S->rp[i]; a < S->rp[i + 1] && !cross; ++a) cross = S->ci[a] / block != bi;
+        for (int64_t a = ST->rp[i]; a < ST->rp[i + 1] && !cross; ++a) cross = ST->ci[a] / block != bi;
+        if (cross) { inU[i] = 1; ++nu; }
+    }
+    while (nu > 0) {
+        /* select: weight beats every remaining strong neighbour (either direction) */
+        for (int64_t i = 0; i < n; ++i) {
+            sel[i] = 0;
+            if (!inU[i]) continue;
+            double wi = (double)(ST->rp[i + 1] - ST->rp[i]) + ora_hash_frac((uint64_t)i);
+            int best = 1;
+            for (int pass = 0; pass < 2 && best; ++pass) {
+                const ora_csr *G = pass == 0 ? S : ST;
+                for (int64_t a = G->rp[i]; a < G->rp[i + 1] && best; ++a) {
+                    int64_t j = G->ci[a];
+                    if (!inU[j]) continue;
+                    double wj = (double)(ST->rp[j + 1] - ST->rp[j]) + ora_hash_frac((uint64_t)j);
+                    if (wj > wi || (wj == wi && j < i)) best = 0;
+                }
+            }
+            sel[i] = (int8_t)best;
+        }
+        for (int64_t i = 0; i < n; ++i)
+            if (sel[i]) { cf[i] = 1; inU[i] = 0; --nu; }
+        for (int64_t i = 0; i < n; ++i)
+            if (inU[i] && has_strong_c(S, cf, i)) { inU[i] = 0; --nu; }
+    }
+    free(inU);
+    free(sel);
     return ORA_OK;
 }
 
@@ -486,7 +571,7 @@ void ora_free(ora_hier *H);
 
 ora_hier *ora_setup(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
                     double theta, double theta_r, int distance, int max_coarse, int max_levels,
-                    int max_dense, const char *relax, double omega, int *status) {
+                    int max_dense, const char *relax, double omega, int64_t falgout_block, int *status) {
     *status = ORA_OK;
     if (n <= 0 || max_levels < 1 || max_levels > ORA_MAX_LEVELS || distance < 1) { *status = ORA_ERR_ARG; return NULL; }
     ora_hier *H = (ora_hier *)calloc(1, sizeof(ora_hier));
@@ -510,7 +595,11 @@ ora_hier *ora_setup(int64_t n, const int64_t *rp, const int32_t *ci, const doubl
         L->cf = (int8_t *)malloc((size_t)nl);
         L->cid = (int32_t *)malloc((size_t)nl * sizeof(int32_t));
         if (!L->cf || !L->cid) { *status = ORA_ERR_OOM; return H; }
-        if ((*status = rs_first_pass(&L->S, &L->ST, L->cf))) return H;
+        if (falgout_block > 0) {
+            if ((*status = falgout_split(&L->S, &L->ST, L->cf, falgout_block))) return H;
+        } else if ((*status = rs_first_pass(&L->S, &L->ST, L->cf))) {
+            return H;
+        }
         int64_t nc = 0;
         for (int64_t i = 0; i < nl; ++i) L->cid[i] = L->cf[i] == 1 ? (int32_t)nc++ : -1;
         L->nc = nc;

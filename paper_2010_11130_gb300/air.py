@@ -40,7 +40,8 @@ class air_options(C.Structure):
     _fields_ = [("theta", C.c_double), ("distance", C.c_int), ("relax", C.c_char * 16),
                 ("omega", C.c_double), ("max_coarse", C.c_int), ("max_levels", C.c_int),
                 ("max_dense", C.c_int), ("precision", C.c_int), ("restart", C.c_int),
-                ("max_iter", C.c_int), ("validate", C.c_int), ("theta_r", C.c_double)]
+                ("max_iter", C.c_int), ("validate", C.c_int), ("theta_r", C.c_double),
+                ("falgout_block", C.c_int)]
 
 
 class air_solve_info(C.Structure):

@@ -178,8 +178,11 @@ int coarsen(air_hierarchy *H, int l, cudaStream_t s, int *stop) {
     // a3 C/F splitting
     T.start(2);
     AIR_TRY(dalloc(&L.cf, n));
-    AIR_TRY(air_rs_first_pass(n, L.srp, L.sci, strp, stci, max_st, max_s, L.cf, H->d_err, rs_cached(), H->d_stats,
-                              s));
+    if (o.falgout_block > 0)
+        AIR_TRY(air_falgout_split(n, o.falgout_block, L.srp, L.sci, strp, stci, L.cf, H->d_err, s));
+    else
+        AIR_TRY(air_rs_first_pass(n, L.srp, L.sci, strp, stci, max_st, max_s, L.cf, H->d_err, rs_cached(),
+                                  H->d_stats, s));
     AIR_TRY(check_err(H, s));
     dfree(strp);
     dfree(stci);
@@ -582,6 +585,7 @@ void air_default_options(air_options *o) {
     o->max_iter = 1000;
     o->validate = 1;
     o->theta_r = -1.0;
+    o->falgout_block = 0;
 }
 
 int air_setup(const air_csr *A, double theta, int distance, const air_options *opt, void *stream,
@@ -599,7 +603,8 @@ int air_setup(const air_csr *A, double theta, int distance, const air_options *o
     for (const char *c = o.relax; *c; ++c)
         if (*c != 'F' && *c != 'C') return AIR_ERR_INVALID_ARG;
     if (!(theta >= 0.0) || !(theta <= 1.0) || !(o.theta_r <= 1.0) || o.max_levels < 1 || o.max_levels > AIR_MAX_LEVELS ||
-        o.max_dense < 1 || o.restart < 1 || o.restart > 32 || o.max_iter < 0 ||
+        o.max_dense < 1 || o.restart < 1 || o.restart > 32 || o.max_iter < 0 || o.falgout_block < 0 ||
+        (o.falgout_block > 0 && (o.falgout_block % 1024 != 0 || o.falgout_block > 8192)) ||
         (o.precision != AIR_PREC_F64 && o.precision != AIR_PREC_F32 && o.precision != AIR_PREC_BF16))
         return AIR_ERR_INVALID_ARG;
     if (distance < 1) return AIR_ERR_INVALID_ARG;

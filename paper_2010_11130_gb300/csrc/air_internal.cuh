@@ -186,6 +186,9 @@ int air_rs_first_pass(int64_t n, const int64_t *srp, const int32_t *sci, const i
 int air_rs_first_pass_cursor(int64_t n, const int64_t *srp, const int32_t *sci, const int64_t *strp,
                              const int32_t *stci, int32_t max_st, int8_t *cf, int *d_err,
                              unsigned long long *stats, cudaStream_t s);
+// falgout.cu: Falgout-style splitting with index blocks of `block` points (a multiple of 1024, <= 8192)
+int air_falgout_split(int64_t n, int64_t block, const int64_t *srp, const int32_t *sci, const int64_t *strp,
+                      const int32_t *stci, int8_t *cf, int *d_err, cudaStream_t s);
 int air_coarse_ids(int64_t n, const int8_t *cf, int32_t *cid, int32_t *crows, int64_t *work, int64_t *nc,
                    cudaStream_t s);
 // distance 1: N_i = S_i intersect F; distance 2 adds S_k intersect F for k in it
