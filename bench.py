@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--rtol", type=float, default=1e-8)
     ap.add_argument("--distance", type=int, default=1, help="l-AIR neighbourhood distance (1 or 2)")
     ap.add_argument("--no-gpu-assembly", action="store_true")
+    ap.add_argument("--autotune", type=int, default=1, help="time the lanes per row of every level at setup")
+    ap.add_argument("--block-size", type=int, default=-1,
+                    help="block form of the finest operator: facet block size b (-1: b of the workload, 0: off)")
     ap.add_argument("--falgout-block", type=int, default=8192,
                     help="block size of the Falgout-style splitting variant reported beside the headline (0: off)")
     ap.add_argument("--workers", type=int, default=min(16, os.cpu_count() or 1))
@@ -61,7 +64,7 @@ def parse():
     ap.add_argument("--vcycles", type=int, default=100)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="single", choices=["single", "batched", "multirhs", "table2", "largest"],
+    ap.add_argument("--workload", default="single", choices=["single", "batched", "multirhs", "table2", "largest", "vcycle"],
                     help="batched: 16 independent uneven problems set up and solved at once")
     ap.add_argument("--large-n", type=int, default=56, help="largest workload: cubes per direction")
     ap.add_argument("--batch-count", type=int, default=16)
@@ -79,12 +82,17 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def block_size(args):
+    return (args.p + 1) * (args.p + 2) // 2 if args.block_size < 0 else args.block_size
+
+
 def workload_config(args):
     n, p = args.n, args.p
     return {"workload": f"st2d_hdg_n{n}_p{p}_rotating_nu{args.nu:g}",
             "mesh": f"{n}^3 cubes x 6 tetrahedra", "p": p, "nu": args.nu, "rtol": args.rtol,
             "unknowns": (12 * n ** 3 - 2 * n * n) * (p + 1) * (p + 2) // 2,
             "theta": 0.25, "distance": args.distance, "relax": "FCF", "restart": 30,
+            "finest_storage": f"facet blocks of {block_size(args)}" if block_size(args) else "entries",
             "l2_flush": "inputs larger than L2 (CSR of A is several GB)"}
 
 
@@ -153,6 +161,9 @@ def vcycle_bytes(H, wbytes, diag_bytes=0):
       F sweep (+P)  z_F (w+4) + 8 n_F + 4 n + w n_C + 2 w n_F + n + w n
       C sweep       z_C (w+4) + 8 n_C + w n + 2 w n_C + n + w n
       F sweep       z_F (w+4) + 8 n_F + w n + 2 w n_F + n + w n
+    A level stored in the block form (facet blocks of b) reads per row set
+    (z - rows) w + 4 (z - rows) / b + x rows for the matrix instead of z (w+4)
+    (the standalone diagonal one per row, in the vector type x).
     coarsest: w n_L^2 + 2 w n_L.  BF16 storage (w = 2) adds the FP32
     diagonal (4 B per relaxed row) and keeps FP32 vectors (counted as w = 4
     for vectors).
@@ -175,10 +186,18 @@ def vcycle_bytes(H, wbytes, diag_bytes=0):
         nf = n - nc
         w = wbytes                       # stored value bytes
         x = 4 if wbytes == 2 else wbytes  # vector element bytes
+        bsz = inf.block_size
+
+        def mat(z, rows):
+            # entry form: value + 4 B column per entry; block form: the b values of every
+            # block with one 4 B column per block, the standalone diagonal in the vector type
+            if not bsz:
+                return z * (w + 4)
+            return (z - rows) * w + (z - rows) // bsz * 4 + rows * x
         total += inf.nnz_r * (w + 4) + 8 * nc + x * n + x * nc
-        total += zf * (w + 4) + 8 * nf + 4 * n + x * nc + 2 * x * nf + n + x * n + diag_bytes * nf
-        total += zc * (w + 4) + 8 * nc + x * n + 2 * x * nc + n + x * n + diag_bytes * nc
-        total += zf * (w + 4) + 8 * nf + x * n + 2 * x * nf + n + x * n + diag_bytes * nf
+        total += mat(zf, nf) + 8 * nf + 4 * n + x * nc + 2 * x * nf + n + x * n + diag_bytes * nf
+        total += mat(zc, nc) + 8 * nc + x * n + 2 * x * nc + n + x * n + diag_bytes * nc
+        total += mat(zf, nf) + 8 * nf + x * n + 2 * x * nf + n + x * n + diag_bytes * nf
     return total
 
 
@@ -414,7 +433,8 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
 
     def step(prec):
-        H = air.setup(A, theta=0.25, distance=args.distance, precision=prec)
+        H = air.setup(A, theta=0.25, distance=args.distance, precision=prec, block_size=block_size(args),
+                      autotune=args.autotune)
         x, info = air.gmres_solve(A, H, b, rtol=args.rtol)
         H.free()
         return info
@@ -459,7 +479,8 @@ def run_ours(args):
     for prec, key in ((1, "f32"), (0, "f64"), (2, "bf16")):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        H = air.setup(A, theta=0.25, distance=args.distance, precision=prec)
+        H = air.setup(A, theta=0.25, distance=args.distance, precision=prec, block_size=block_size(args),
+                      autotune=args.autotune)
         t_setup = time.perf_counter() - t0
         xs = torch.empty_like(b)
         torch.cuda.synchronize()
@@ -486,6 +507,8 @@ def run_ours(args):
             H.vcycle(b, xv)
         t = median_time(lambda: H.vcycle(b, xv), stream, args.vcycles)
         rl[key] = {"bytes": vb, "s": t, "gbs": vb / t / 1e9, "levels": H.levels(),
+                   "lanes_per_row": [[H.info(l).lanes_f, H.info(l).lanes_c, H.info(l).lanes_r]
+                                     for l in range(H.levels() - 1)],
                    "timing": f"median of 5 runs of {args.vcycles} V-cycles (CUDA-graph replays)"}
         H.free()
     y = torch.empty_like(b)
@@ -498,7 +521,8 @@ def run_ours(args):
     falgout = None
     if args.falgout_block > 0:
         def fstep():
-            H = air.setup(A, theta=0.25, distance=args.distance, precision=1, falgout_block=args.falgout_block)
+            H = air.setup(A, theta=0.25, distance=args.distance, precision=1, falgout_block=args.falgout_block,
+                          block_size=block_size(args), autotune=args.autotune)
             x, info = air.gmres_solve(A, H, b, rtol=args.rtol)
             ph = H.setup_timings()
             lv = H.levels()
@@ -538,7 +562,8 @@ def run_ours(args):
         tt = []
         for _ in range(1):
             t0 = time.perf_counter()
-            Hh = air.setup(Ah, theta=0.25, distance=args.distance, precision=1)
+            Hh = air.setup(Ah, theta=0.25, distance=args.distance, precision=1, block_size=block_size(args),
+                           autotune=args.autotune)
             _, ih = air.gmres_solve(Ah, Hh, b_h, x_h, rtol=args.rtol)
             Hh.free()
             tt.append(time.perf_counter() - t0)
@@ -847,6 +872,28 @@ def run_largest(args):
     print(json.dumps(out), flush=True)
 
 
+def run_vcycle(args):
+    """V-cycles alone on the workload family (the profiling target): FP32
+    hierarchy (block form of the finest operator), 3 warm-up V-cycles, then
+    --vcycles timed ones; prints the algorithmic bytes, the time and GB/s."""
+    import torch
+    import paper_2010_11130_gb300 as air
+    air.build()
+    s = make_system(args)
+    A = air.CSR.from_host(s.row_ptr, s.col, s.val)
+    b = torch.from_numpy(np.ascontiguousarray(s.rhs)).cuda()
+    H = air.setup(A, theta=0.25, distance=args.distance, precision=1, block_size=block_size(args),
+                  autotune=args.autotune)
+    vb = vcycle_bytes(H, 4)
+    x = torch.empty_like(b)
+    for _ in range(3):
+        H.vcycle(b, x)
+    t = median_time(lambda: H.vcycle(b, x), torch.cuda.current_stream(), args.vcycles, runs=1)
+    print(json.dumps({"workload": workload_config(args)["workload"], "vcycle_bytes": vb, "vcycle_s": t,
+                      "gbs": vb / t / 1e9, "levels": H.levels(),
+                      "level_sizes": [int(H.info(l).n) for l in range(H.levels())]}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -859,6 +906,8 @@ def main():
         run_table2(args)
     elif args.workload == "largest":
         run_largest(args)
+    elif args.workload == "vcycle":
+        run_vcycle(args)
     else:
         run_ours(args)
 

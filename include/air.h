@@ -78,6 +78,17 @@ typedef struct {
                             restricted to the block, and interface points left F without a strong
                             C point are fixed by rounds of a parallel independent set (weight
                             |S^T_i| plus a SplitMix64 fraction of i) */
+    int block_size;      /* 0: every level stored entry by entry; b in {2, 3, 4, 6, 10}: when every
+                            row of the finest operator is whole aligned b-blocks of consecutive
+                            columns plus at most its diagonal (the facet blocks of the trace
+                            system), its relaxation sweeps and the Krylov matrix products use a
+                            block form (one column index per block, the block's values read as
+                            runs); otherwise, or for other b, the entry form */
+    int autotune;        /* lanes per row of the entry-form sweeps and restriction on each level:
+                            0: by a rule on the stored row width; 1: the fastest of 1, 2, 4, ..., 32
+                            lanes, timed with CUDA events at the end of air_setup (about a hundred
+                            launches; the choice can differ between runs, and the V-cycle's
+                            results with it in the last bits) */
 } air_options;
 
 typedef struct {
@@ -96,13 +107,18 @@ typedef struct {
     int64_t n_singular;  /* l-AIR local systems treated as singular (injection rows) */
     int32_t max_m;       /* largest l-AIR local system */
     int32_t coarsest;    /* 1 on the last level */
+    int32_t block_size;  /* b when the level's relaxation uses the block form, else 0 */
+    int32_t lanes_f;     /* lanes per row of the F sweep, the C sweep and the restriction */
+    int32_t lanes_c;     /* (entry form; 1 = one thread per row) */
+    int32_t lanes_r;
 } air_level_info;
 
 typedef struct air_hierarchy air_hierarchy;   /* opaque, library-owned */
 
 /* Fill *opt with the defaults: theta 0.25, distance 1, relax "FCF", omega 1,
  * max_coarse 1000, max_levels 25, max_dense 4096, AIR_PREC_F64, restart 30,
- * max_iter 1000, validate 1, theta_r -1 (same as theta), falgout_block 0. */
+ * max_iter 1000, validate 1, theta_r -1 (same as theta), falgout_block 0, block_size 0,
+ * autotune 0. */
 void air_default_options(air_options *opt);
 
 /* Build the l-AIR hierarchy of A (Section 3; Section 4 solver settings):

@@ -41,7 +41,7 @@ class air_options(C.Structure):
                 ("omega", C.c_double), ("max_coarse", C.c_int), ("max_levels", C.c_int),
                 ("max_dense", C.c_int), ("precision", C.c_int), ("restart", C.c_int),
                 ("max_iter", C.c_int), ("validate", C.c_int), ("theta_r", C.c_double),
-                ("falgout_block", C.c_int)]
+                ("falgout_block", C.c_int), ("block_size", C.c_int), ("autotune", C.c_int)]
 
 
 class air_solve_info(C.Structure):
@@ -52,7 +52,8 @@ class air_solve_info(C.Structure):
 class air_level_info(C.Structure):
     _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("nnz_s", C.c_int64), ("nc", C.c_int64),
                 ("nnz_r", C.c_int64), ("n_singular", C.c_int64), ("max_m", C.c_int32),
-                ("coarsest", C.c_int32)]
+                ("coarsest", C.c_int32), ("block_size", C.c_int32), ("lanes_f", C.c_int32),
+                ("lanes_c", C.c_int32), ("lanes_r", C.c_int32)]
 
 
 class air_hdg_mesh(C.Structure):

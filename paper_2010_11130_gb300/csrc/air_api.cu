@@ -359,8 +359,29 @@ int setup_impl(const air_csr *A, const air_options *opt, cudaStream_t s, air_hie
                 AIR_TRY(dalloc(&L.diag32, L.n));
                 AIR_TRY(air_cast_bf16(L.n, L.rp, L.ci, L.v, nullptr, L.diag32, s));
             }
-            AIR_TRY(air_build_sell(L.nf, L.frows, L.rp, L.ci, L.v, opt->precision, bf16, &L.sset[0], s));
-            AIR_TRY(air_build_sell(L.nc, L.crows, L.rp, L.ci, L.v, opt->precision, bf16, &L.sset[1], s));
+            // level 0 of a matrix made of b x b blocks: the block form, else entries
+            bool blocked = false;
+            if (q == 0 && opt->block_size > 0) {
+                Sell bf, bcs;
+                int s0 = air_build_sell_blocks(L.nf, L.frows, L.rp, L.ci, L.v, opt->precision, opt->block_size, &bf, s);
+                int s1 = s0 == AIR_OK ? air_build_sell_blocks(L.nc, L.crows, L.rp, L.ci, L.v, opt->precision,
+                                                              opt->block_size, &bcs, s)
+                                      : s0;
+                if (s0 == AIR_OK && s1 == AIR_OK) {
+                    L.sset[0] = bf;
+                    L.sset[1] = bcs;
+                    blocked = true;
+                } else {
+                    air_free_sell(bf);
+                    air_free_sell(bcs);
+                    if ((s0 != AIR_OK && s0 != AIR_ERR_UNSUPPORTED) || (s1 != AIR_OK && s1 != AIR_ERR_UNSUPPORTED))
+                        return s0 != AIR_OK ? s0 : s1;
+                }
+            }
+            if (!blocked) {
+                AIR_TRY(air_build_sell(L.nf, L.frows, L.rp, L.ci, L.v, opt->precision, bf16, &L.sset[0], s));
+                AIR_TRY(air_build_sell(L.nc, L.crows, L.rp, L.ci, L.v, opt->precision, bf16, &L.sset[1], s));
+            }
             AIR_TRY(air_build_sell(L.nc, nullptr, L.rrp, L.rci, L.rv, opt->precision, 0, &L.sr, s));
         }
         size_t es = f32 ? sizeof(float) : sizeof(double);
@@ -370,12 +391,20 @@ int setup_impl(const air_csr *A, const air_options *opt, cudaStream_t s, air_hie
     }
     {
         AirLevel &L0 = H->lev[0];
-        AIR_TRY(air_build_sell(L0.n, nullptr, L0.rp, L0.ci, L0.v, AIR_PREC_F64, 0, &H->a0, s));
+        int sb = opt->block_size > 0
+                     ? air_build_sell_blocks(L0.n, nullptr, L0.rp, L0.ci, L0.v, AIR_PREC_F64, opt->block_size, &H->a0, s)
+                     : AIR_ERR_UNSUPPORTED;
+        if (sb != AIR_OK) {
+            air_free_sell(H->a0);
+            if (sb != AIR_ERR_UNSUPPORTED) return sb;
+            AIR_TRY(air_build_sell(L0.n, nullptr, L0.rp, L0.ci, L0.v, AIR_PREC_F64, 0, &H->a0, s));
+        }
     }
     if (f32) {
         AIR_TRY(dalloc(&H->cinv32, H->nco * H->nco));
         AIR_TRY(air_cast_d2f(H->cinv, H->cinv32, H->nco * H->nco, s));
     }
+    AIR_TRY(air_tune_lanes(H, opt->autotune, s));
     AIR_CUDA(cudaStreamSynchronize(s));
     return AIR_OK;
 }
@@ -586,6 +615,8 @@ void air_default_options(air_options *o) {
     o->validate = 1;
     o->theta_r = -1.0;
     o->falgout_block = 0;
+    o->block_size = 0;
+    o->autotune = 0;
 }
 
 int air_setup(const air_csr *A, double theta, int distance, const air_options *opt, void *stream,
@@ -604,7 +635,8 @@ int air_setup(const air_csr *A, double theta, int distance, const air_options *o
         if (*c != 'F' && *c != 'C') return AIR_ERR_INVALID_ARG;
     if (!(theta >= 0.0) || !(theta <= 1.0) || !(o.theta_r <= 1.0) || o.max_levels < 1 || o.max_levels > AIR_MAX_LEVELS ||
         o.max_dense < 1 || o.restart < 1 || o.restart > 32 || o.max_iter < 0 || o.falgout_block < 0 ||
-        (o.falgout_block > 0 && (o.falgout_block % 1024 != 0 || o.falgout_block > 8192)) ||
+        (o.falgout_block > 0 && (o.falgout_block % 1024 != 0 || o.falgout_block > 8192)) || o.block_size < 0 ||
+        o.block_size > 16 ||
         (o.precision != AIR_PREC_F64 && o.precision != AIR_PREC_F32 && o.precision != AIR_PREC_BF16))
         return AIR_ERR_INVALID_ARG;
     if (distance < 1) return AIR_ERR_INVALID_ARG;
@@ -793,6 +825,10 @@ int air_hierarchy_info(const air_hierarchy *H, int level, air_level_info *info) 
     info->n_singular = L.n_singular;
     info->max_m = L.max_m;
     info->coarsest = level == H->nlev - 1;
+    info->block_size = L.sset[0].b > 0 ? L.sset[0].b : L.sset[1].b;
+    info->lanes_f = L.lanes[0];
+    info->lanes_c = L.lanes[1];
+    info->lanes_r = L.lanes[2];
     return AIR_OK;
 }
 

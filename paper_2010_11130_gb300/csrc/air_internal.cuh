@@ -74,13 +74,25 @@ void air_dfree(void *p);
 // ptr[s] + 32 k + l.  A slice is as wide as its longest row; shorter rows are
 // padded with zero values (column = the row itself).  Values are in the
 // V-cycle's storage type.
+//
+// Block form (b > 0): rows made of whole aligned b-blocks of consecutive
+// columns plus at most a standalone diagonal entry (the level-0 trace matrix:
+// facet blocks, the scaled diagonal block stored as its ones).  Then ptr
+// counts stored blocks: slot t of lane l holds the block's first column
+// bc[ptr[s] + 32 t + l] and its b values at v + (ptr[s] + 32 t + l) b; dv[pos]
+// is the standalone diagonal in the vector type (0 when the diagonal sits in
+// a block; for BF16 storage the diagonal is always zeroed in the blocks and
+// kept in dv in FP32).  Padding slots: column 0 with zero values.
 struct Sell {
     int64_t m = 0;              // rows
     int32_t *rows = nullptr;    // pos -> row id (rows sorted by length inside windows of 1024)
     int64_t *ptr = nullptr;     // m / 32 + 1 slice offsets
     int32_t *ci = nullptr;
     void *v = nullptr;
-    int64_t stored = 0;         // entries including padding
+    int64_t stored = 0;         // entries (block form: blocks) including padding
+    int b = 0;                  // block size of the block form, 0 for entries
+    int32_t *bc = nullptr;      // block form: first column of each stored block
+    void *dv = nullptr;         // block form: standalone diagonal per position
 };
 
 struct AirLevel {
@@ -118,6 +130,9 @@ struct AirLevel {
     // (0 = F, 1 = C) for the relaxation sweeps, and R_l for the restriction
     Sell sset[2];
     Sell sr;
+    // lanes per row of the entry-form kernels: F sweep, C sweep, restriction
+    // (1: one thread per row; more: the row's entries split over that many lanes)
+    int lanes[3] = {1, 1, 1};
     // V-cycle work vectors (precision of the hierarchy)
     void *b = nullptr, *x = nullptr, *x2 = nullptr;
 };
@@ -237,8 +252,17 @@ int air_cast_bf16(int64_t n, const int64_t *rp, const int32_t *ci, const double 
                   cudaStream_t s);
 int air_build_sell(int64_t m, const int32_t *rows, const int64_t *rp, const int32_t *ci, const double *v,
                    int precision, int zero_diag, Sell *out, cudaStream_t s);
+// The block form of the same rows with block size b (2, 3, 4, 6 or 10).
+// AIR_ERR_UNSUPPORTED (out left empty, nothing else changed) when a row is not
+// whole aligned blocks plus at most its diagonal.
+int air_build_sell_blocks(int64_t m, const int32_t *rows, const int64_t *rp, const int32_t *ci, const double *v,
+                          int precision, int b, Sell *out, cudaStream_t s);
 void air_free_sell(Sell &S);
 int air_sell_spmv_f64(const Sell &S, const double *x, double *y, const double *b, cudaStream_t s);
+// Lanes per row for every level's sweeps and restriction: a rule on the
+// stored row width, or (timed = 1) the fastest of 1, 2, 4, 8, 16, 32 lanes
+// timed with CUDA events on the level's own data.
+int air_tune_lanes(air_hierarchy *H, int timed, cudaStream_t s);
 int air_diag_inverse(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, double *dinv,
                      float *dinv32, cudaStream_t s);
 

@@ -292,9 +292,184 @@ __global__ void __launch_bounds__(256) sell_kernel(SellArgs<TV, TX> a) {
     }
 }
 
+// ------------------------------------------------------- block SELL-32
+// Loads of b consecutive values: pairs when b is even and the start is
+// aligned to a pair (2 b-element rows of float / double / bf16 keep that
+// alignment when the base is aligned), scalars otherwise.
+template <typename T>
+struct Pair;
+template <>
+struct Pair<double> { using type = double2; };
+template <>
+struct Pair<float> { using type = float2; };
+template <>
+struct Pair<__nv_bfloat16> { using type = __nv_bfloat162; };
+
+template <typename A, typename T>
+__device__ __forceinline__ void pair_to(const typename Pair<T>::type &p, A &a0, A &a1) {
+    a0 = (A)p.x;
+    a1 = (A)p.y;
+}
+template <>
+__device__ __forceinline__ void pair_to<float, __nv_bfloat16>(const __nv_bfloat162 &p, float &a0, float &a1) {
+    a0 = __bfloat162float(p.x);
+    a1 = __bfloat162float(p.y);
+}
+
+template <int B, bool PAIRS, typename A, typename T>
+__device__ __forceinline__ void load_run(const T *__restrict__ p, A (&out)[B]) {
+    if constexpr (PAIRS && B % 2 == 0) {
+        const typename Pair<T>::type *q = reinterpret_cast<const typename Pair<T>::type *>(p);
+#pragma unroll
+        for (int j = 0; j < B / 2; ++j) pair_to<A, T>(__ldg(q + j), out[2 * j], out[2 * j + 1]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < B; ++j) out[j] = to_acc<A, T>(__ldg(p + j));
+    }
+}
+
+template <typename TV, typename TX>
+struct BSellArgs {
+    int64_t m;
+    const int64_t *ptr;
+    const int32_t *bc;
+    const TV *v;
+    const TX *dv;
+    const int32_t *rows;
+    const TX *x;
+    TX *y;
+    const TX *b;
+    const TX *dinv;
+    TX omega;
+};
+
+// One thread per row: the row's blocks two at a time, each block's b values
+// and b entries of x as runs of consecutive elements.
+template <int B, bool PAIRS, typename TV, typename TX, int MODE>
+__global__ void __launch_bounds__(256) bsell_kernel(BSellArgs<TV, TX> a) {
+    using A = typename Acc<TX>::type;
+    const int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (pos >= a.m) return;
+    const int64_t sl = pos >> 5;
+    const int l = (int)(pos & 31);
+    const int64_t base = a.ptr[sl];
+    const int w = (int)((a.ptr[sl + 1] - base) >> 5);
+    const int64_t row = a.rows[pos];
+    A acc = (A)a.dv[pos] * (A)a.x[row];
+    int t = 0;
+    for (; t + 2 <= w; t += 2) {
+        const int64_t i0 = base + 32 * t + l, i1 = i0 + 32;
+        const int32_t c0 = __ldg(a.bc + i0), c1 = __ldg(a.bc + i1);
+        A v0[B], v1[B], x0[B], x1[B];
+        load_run<B, PAIRS>(a.v + i0 * B, v0);
+        load_run<B, PAIRS>(a.v + i1 * B, v1);
+        load_run<B, PAIRS>(a.x + c0, x0);
+        load_run<B, PAIRS>(a.x + c1, x1);
+#pragma unroll
+        for (int j = 0; j < B; ++j) acc += v0[j] * x0[j];
+#pragma unroll
+        for (int j = 0; j < B; ++j) acc += v1[j] * x1[j];
+    }
+    if (t < w) {
+        const int64_t i0 = base + 32 * t + l;
+        const int32_t c0 = __ldg(a.bc + i0);
+        A v0[B], x0[B];
+        load_run<B, PAIRS>(a.v + i0 * B, v0);
+        load_run<B, PAIRS>(a.x + c0, x0);
+#pragma unroll
+        for (int j = 0; j < B; ++j) acc += v0[j] * x0[j];
+    }
+    if (MODE == ROW_SPMV) {
+        a.y[row] = a.b ? (TX)((A)a.b[row] - acc) : (TX)acc;
+    } else {
+        a.y[pos] = (TX)(a.x[row] + a.omega * ((TX)((A)a.b[row] - acc)) * a.dinv[row]);
+    }
+}
+
+template <int B, typename TV, typename TX, int MODE>
+void bsell_launch_b(const BSellArgs<TV, TX> &a, bool pairs, cudaStream_t s) {
+    const unsigned g = (unsigned)((a.m + 255) / 256);
+    if (pairs) bsell_kernel<B, true, TV, TX, MODE><<<air_counted(g), 256, 0, s>>>(a);
+    else bsell_kernel<B, false, TV, TX, MODE><<<air_counted(g), 256, 0, s>>>(a);
+}
+
+// pairs are safe when x starts on a pair boundary (the values always do)
 template <typename TV, typename TX, int MODE>
-void sell_launch(const SellArgs<TV, TX> &a, cudaStream_t s) {
+void bsell_launch(int b, const BSellArgs<TV, TX> &a, cudaStream_t s) {
     if (a.m <= 0) return;
+    const bool pairs = ((uintptr_t)a.x % (2 * sizeof(TX))) == 0;
+    switch (b) {
+    case 2: bsell_launch_b<2, TV, TX, MODE>(a, pairs, s); break;
+    case 3: bsell_launch_b<3, TV, TX, MODE>(a, pairs, s); break;
+    case 4: bsell_launch_b<4, TV, TX, MODE>(a, pairs, s); break;
+    case 6: bsell_launch_b<6, TV, TX, MODE>(a, pairs, s); break;
+    default: bsell_launch_b<10, TV, TX, MODE>(a, pairs, s); break;
+    }
+}
+
+// VL lanes per row (VL divides 32): lane j of a row takes the row's stored
+// entries j, j + VL, ..., four at a time, then the lanes sum their partial
+// results.  For levels whose rows are long (Galerkin fill) and few, the row's
+// latency chain is VL times shorter.
+template <int VL, typename TV, typename TX, int MODE>
+__global__ void __launch_bounds__(256) sell_lanes_kernel(SellArgs<TV, TX> a) {
+    using A = typename Acc<TX>::type;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t pos = t / VL;
+    const int j = (int)(t % VL);
+    const bool valid = pos < a.m;                 // whole groups of VL lanes share validity
+    A acc = 0;
+    int64_t row = 0;
+    if (valid) {
+        const int64_t sl = pos >> 5;
+        const int l = (int)(pos & 31);
+        const int64_t base = a.ptr[sl];
+        const int w = (int)((a.ptr[sl + 1] - base) >> 5);
+        const int32_t *cp = a.ci + base + l;
+        const TV *vp = a.v + base + l;
+        int k = j;
+        for (; k + 3 * VL < w; k += 4 * VL) {
+            int32_t c[4];
+            TV vv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                c[u] = __ldg(cp + 32 * (k + u * VL));
+                vv[u] = vp[32 * (k + u * VL)];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc += to_acc<A, TV>(vv[u]) * (A)__ldg(a.x + c[u]);
+        }
+        for (; k < w; k += VL) acc += to_acc<A, TV>(vp[32 * k]) * (A)__ldg(a.x + cp[32 * k]);
+        row = a.rows[pos];
+    }
+#pragma unroll
+    for (int o = VL / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o, VL);
+    if (!valid || j != 0) return;
+    if (MODE == ROW_SPMV) {
+        a.y[row] = a.b ? (TX)((A)a.b[row] - acc) : (TX)acc;
+    } else {
+        if (a.diag) acc += (A)a.diag[row] * (A)a.x[row];
+        a.y[pos] = (TX)(a.x[row] + a.omega * ((TX)((A)a.b[row] - acc)) * a.dinv[row]);
+    }
+}
+
+template <int VL, typename TV, typename TX, int MODE>
+void sell_lanes_launch(const SellArgs<TV, TX> &a, cudaStream_t s) {
+    const unsigned g = (unsigned)((a.m * VL + 255) / 256);
+    sell_lanes_kernel<VL, TV, TX, MODE><<<air_counted(g), 256, 0, s>>>(a);
+}
+
+template <typename TV, typename TX, int MODE>
+void sell_launch(const SellArgs<TV, TX> &a, cudaStream_t s, int lanes = 1) {
+    if (a.m <= 0) return;
+    switch (lanes) {
+    case 2: sell_lanes_launch<2, TV, TX, MODE>(a, s); return;
+    case 4: sell_lanes_launch<4, TV, TX, MODE>(a, s); return;
+    case 8: sell_lanes_launch<8, TV, TX, MODE>(a, s); return;
+    case 16: sell_lanes_launch<16, TV, TX, MODE>(a, s); return;
+    case 32: sell_lanes_launch<32, TV, TX, MODE>(a, s); return;
+    default: break;
+    }
     unsigned g = (unsigned)((a.m + 255) / 256);
     sell_kernel<8, TV, TX, MODE><<<air_counted(g), 256, 0, s>>>(a);
 }
@@ -514,10 +689,18 @@ void jacobi_dispatch(const AirLevel &L, const T *diag, const T *dinv, int which,
                      cudaStream_t s) {
     const Sell &S = L.sset[which];
     if (S.m == 0) return;
+    if (S.b > 0) {
+        BSellArgs<TV, T> ba{};
+        ba.m = S.m; ba.ptr = S.ptr; ba.bc = S.bc; ba.v = (const TV *)S.v; ba.dv = (const T *)S.dv; ba.rows = S.rows;
+        ba.x = x; ba.y = tmp; ba.b = b; ba.dinv = dinv; ba.omega = omega;
+        bsell_launch<TV, T, ROW_JACOBI>(S.b, ba, s);
+        scatter_kernel<T><<<air_counted(grid_cap(S.m, 256)), 256, 0, s>>>(S.m, S.rows, tmp, x);
+        return;
+    }
     SellArgs<TV, T> a{};
     a.m = S.m; a.ptr = S.ptr; a.ci = S.ci; a.v = (const TV *)S.v; a.rows = S.rows;
     a.x = x; a.y = tmp; a.b = b; a.dinv = dinv; a.diag = diag; a.omega = omega;
-    sell_launch<TV, T, ROW_JACOBI>(a, s);
+    sell_launch<TV, T, ROW_JACOBI>(a, s, L.lanes[which]);
     scatter_kernel<T><<<air_counted(grid_cap(S.m, 256)), 256, 0, s>>>(S.m, S.rows, tmp, x);
 }
 
@@ -544,7 +727,7 @@ int vcycle_t(const air_hierarchy *H, const T *b0, T *x0, cudaStream_t s) {
         SellArgs<TV, T> ra{};
         ra.m = A.sr.m; ra.ptr = A.sr.ptr; ra.ci = A.sr.ci; ra.v = (const TV *)A.sr.v; ra.rows = A.sr.rows;
         ra.x = bl; ra.y = (T *)H->lev[l + 1].b;
-        sell_launch<TV, T, ROW_SPMV>(ra, s);
+        sell_launch<TV, T, ROW_SPMV>(ra, s, A.lanes[2]);
     }
     // coarsest: x = A_L^{-1} b
     {
@@ -696,10 +879,263 @@ void air_free_sell(Sell &S) {
     air_dfree(S.ptr);
     air_dfree(S.ci);
     air_dfree(S.v);
+    air_dfree(S.bc);
+    air_dfree(S.dv);
     S = Sell();
 }
 
+// Blocks of each row (pos order of rows_in, or rows 0.. when NULL) into nb[pos];
+// a row that is not whole aligned b-blocks plus at most its diagonal sets *err.
+__global__ void block_count_kernel(int64_t m, const int32_t *rows, const int64_t *rp, const int32_t *ci, int b,
+                                   int32_t *nb, int *err) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < m; p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = rows ? rows[p] : p;
+        int64_t k = rp[r];
+        const int64_t e = rp[r + 1];
+        int cnt = 0;
+        while (k < e) {
+            const int32_t c = ci[k];
+            if (c % b == 0 && k + b <= e && ci[k + b - 1] == c + b - 1) { ++cnt; k += b; }
+            else if (c == r) { ++k; }
+            else { atomicOr(err, 1); break; }
+        }
+        nb[p] = cnt;
+    }
+}
+
+__global__ void block_width_kernel(int64_t m, const int32_t *sorted, const int32_t *pos_of, const int32_t *nb,
+                                   int32_t *wid) {
+    const int64_t ns = (m + 31) / 32;
+    for (int64_t sl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; sl < ns; sl += (int64_t)gridDim.x * blockDim.x) {
+        int32_t w = 0;
+        for (int64_t p = sl * 32; p < m && p < sl * 32 + 32; ++p) w = max(w, nb[pos_of[p]]);
+        wid[sl] = w * 32;
+    }
+}
+
+// position in the unsorted set of every sorted position (rows are distinct)
+__global__ void block_posmap_kernel(int64_t m, const int32_t *rows_in, const int32_t *sorted, int32_t *inv_row,
+                                    int32_t *pos_of) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < m; p += (int64_t)gridDim.x * blockDim.x)
+        pos_of[p] = inv_row[sorted[p]];
+}
+
+__global__ void block_invrow_kernel(int64_t m, const int32_t *rows_in, int32_t *inv_row) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < m; p += (int64_t)gridDim.x * blockDim.x)
+        inv_row[rows_in ? rows_in[p] : p] = (int32_t)p;
+}
+
+template <typename TV, typename TD, bool ZERO_DIAG>
+__global__ void block_fill_kernel(int64_t m, const int32_t *rows, const int64_t *rp, const int32_t *ci,
+                                  const double *v, int b, const int64_t *ptr, int32_t *bc, TV *bv, TD *dv) {
+    const int64_t ns32 = ((m + 31) / 32) * 32;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < ns32; p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t sl = p >> 5, l = p & 31;
+        const int64_t base = ptr[sl], w = (ptr[sl + 1] - base) >> 5;
+        int64_t t = 0;
+        if (p < m) {
+            const int64_t r = rows[p];
+            int64_t k = rp[r];
+            const int64_t e = rp[r + 1];
+            double dstand = 0.0, dall = 0.0;    // standalone diagonal; the diagonal wherever it is
+            while (k < e && t < w) {
+                const int32_t c = ci[k];
+                if (c % b == 0 && k + b <= e && ci[k + b - 1] == c + b - 1) {
+                    const int64_t slot = base + 32 * t + l;
+                    bc[slot] = c;
+                    for (int j = 0; j < b; ++j) {
+                        const bool dg = c + j == r;
+                        if (dg) dall = v[k + j];
+                        bv[slot * b + j] = (TV)((ZERO_DIAG && dg) ? 0.0 : v[k + j]);
+                    }
+                    ++t;
+                    k += b;
+                } else {                         // the standalone diagonal (the structure check passed)
+                    dstand = v[k];
+                    dall = v[k];
+                    ++k;
+                }
+            }
+            if (k < e && ci[k] == r) {           // a standalone diagonal after the last block
+                dstand = v[k];
+                dall = v[k];
+            }
+            dv[p] = (TD)(ZERO_DIAG ? dall : dstand);
+        }
+        for (; t < w; ++t) {
+            const int64_t slot = base + 32 * t + l;
+            bc[slot] = 0;
+            for (int j = 0; j < b; ++j) bv[slot * b + j] = (TV)0.0;
+        }
+    }
+}
+
+namespace {
+
+// Lanes per row by rule: double the lanes while the grid holds fewer than
+// about two waves of threads (or rows longer than 32 stored entries per lane)
+// and each lane keeps more than four entries.
+int lanes_rule(const Sell &S) {
+    if (S.m <= 0 || S.b > 0) return 1;
+    const double avg = (double)S.stored / (double)S.m;
+    int L = 1;
+    while (L < 32 && avg / L > 4.0 && ((double)S.m * L < 152.0 * 2048.0 || avg / L > 32.0)) L *= 2;
+    return L;
+}
+
+template <typename TV, typename T>
+int tune_set(const AirLevel &Lv, const Sell &S, bool jacobi, const T *x, const T *b, T *y, const T *dinv,
+             const T *diag, int *out, cudaStream_t s) {
+    SellArgs<TV, T> a{};
+    a.m = S.m; a.ptr = S.ptr; a.ci = S.ci; a.v = (const TV *)S.v; a.rows = S.rows;
+    a.x = x; a.y = y; a.b = b; a.dinv = dinv; a.diag = diag; a.omega = (T)1;
+    const int cand_all[6] = {1, 2, 4, 8, 16, 32};
+    const double avg = S.m > 0 ? (double)S.stored / (double)S.m : 0.0;
+    cudaEvent_t e0, e1;
+    AIR_CUDA(cudaEventCreate(&e0));
+    AIR_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int pick = 1;
+    for (int c : cand_all) {
+        if (c > 1 && (avg / c < 1.0 || (S.m >= 2000000 && c > 2))) continue;
+        for (int rep = 0; rep < 4; ++rep) {
+            if (rep == 1) cudaEventRecord(e0, s);
+            if (jacobi) sell_launch<TV, T, ROW_JACOBI>(a, s, c);
+            else sell_launch<TV, T, ROW_SPMV>(a, s, c);
+        }
+        cudaEventRecord(e1, s);
+        AIR_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        AIR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) { best = ms; pick = c; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    AIR_LAUNCH();
+    *out = pick;
+    return AIR_OK;
+}
+
+template <typename TV, typename T>
+int tune_levels(air_hierarchy *H, cudaStream_t s) {
+    for (int q = 0; q + 1 < H->nlev; ++q) {
+        AirLevel &L = H->lev[q];
+        const size_t es = sizeof(T);
+        AIR_CUDA(cudaMemsetAsync(L.b, 0, (size_t)L.n * es, s));
+        AIR_CUDA(cudaMemsetAsync(L.x, 0, (size_t)L.n * es, s));
+        const T *dinv = lvl_dinv<T>(L);
+        const T *diag = (const T *)lvl_diag<TV>(L);
+        for (int which = 0; which < 2; ++which)
+            if (L.sset[which].b == 0 && L.sset[which].m > 0)
+                AIR_TRY((tune_set<TV, T>(L, L.sset[which], true, (const T *)L.x, (const T *)L.b, (T *)L.x2, dinv,
+                                         diag, &L.lanes[which], s)));
+        if (L.sr.m > 0)
+            AIR_TRY((tune_set<TV, T>(L, L.sr, false, (const T *)L.b, nullptr, (T *)H->lev[q + 1].b, nullptr, nullptr,
+                                     &L.lanes[2], s)));
+    }
+    return AIR_OK;
+}
+
+}  // namespace
+
+int air_tune_lanes(air_hierarchy *H, int timed, cudaStream_t s) {
+    for (int q = 0; q + 1 < H->nlev; ++q) {
+        AirLevel &L = H->lev[q];
+        L.lanes[0] = lanes_rule(L.sset[0]);
+        L.lanes[1] = lanes_rule(L.sset[1]);
+        L.lanes[2] = lanes_rule(L.sr);
+    }
+    if (!timed) return AIR_OK;
+    if (H->opt.precision == AIR_PREC_F64) return tune_levels<double, double>(H, s);
+    if (H->opt.precision == AIR_PREC_F32) return tune_levels<float, float>(H, s);
+    return tune_levels<__nv_bfloat16, float>(H, s);
+}
+
+int air_build_sell_blocks(int64_t m, const int32_t *rows_in, const int64_t *rp, const int32_t *ci, const double *v,
+                          int precision, int b, Sell *out, cudaStream_t s) {
+    if (b != 2 && b != 3 && b != 4 && b != 6 && b != 10) return AIR_ERR_UNSUPPORTED;
+    *out = Sell();
+    if (m <= 0) return AIR_ERR_UNSUPPORTED;
+    int32_t *nb = nullptr, *inv = nullptr, *pos_of = nullptr, *wid = nullptr;
+    int *err = nullptr;
+    const int64_t ns = (m + 31) / 32;
+    // rows_in are row ids of the level; inverse map sized by the largest id + 1 (<= the level's rows)
+    int64_t idmax = m;
+    if (rows_in) {
+        int32_t hmax = 0;
+        int32_t *dmax = nullptr;
+        AIR_CUDA(cudaMallocAsync(&dmax, sizeof(int32_t), s));
+        AIR_CUDA(cudaMemsetAsync(dmax, 0, sizeof(int32_t), s));
+        AIR_TRY(air_reduce_max_i32(rows_in, m, dmax, s));
+        AIR_CUDA(cudaMemcpyAsync(&hmax, dmax, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        AIR_CUDA(cudaStreamSynchronize(s));
+        cudaFreeAsync(dmax, s);
+        idmax = (int64_t)hmax + 1;
+    }
+    AIR_CUDA(cudaMallocAsync(&nb, (size_t)m * sizeof(int32_t), s));
+    AIR_CUDA(cudaMallocAsync(&err, sizeof(int), s));
+    AIR_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+    block_count_kernel<<<air_counted(grid_cap(m, 256)), 256, 0, s>>>(m, rows_in, rp, ci, b, nb, err);
+    AIR_LAUNCH();
+    int herr = 0;
+    AIR_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    AIR_CUDA(cudaStreamSynchronize(s));
+    cudaFreeAsync(err, s);
+    if (herr) {
+        cudaFreeAsync(nb, s);
+        return AIR_ERR_UNSUPPORTED;
+    }
+    out->m = m;
+    out->b = b;
+    AIR_CUDA(air_dmalloc((void **)&out->rows, (size_t)m * sizeof(int32_t)));
+    sell_sort_kernel<<<air_counted((unsigned)((m + SIGMA - 1) / SIGMA)), SIGMA / 2, 0, s>>>(m, rows_in, rp, out->rows);
+    AIR_LAUNCH();
+    AIR_CUDA(cudaMallocAsync(&inv, (size_t)idmax * sizeof(int32_t), s));
+    AIR_CUDA(cudaMallocAsync(&pos_of, (size_t)m * sizeof(int32_t), s));
+    block_invrow_kernel<<<air_counted(grid_cap(m, 256)), 256, 0, s>>>(m, rows_in, inv);
+    block_posmap_kernel<<<air_counted(grid_cap(m, 256)), 256, 0, s>>>(m, rows_in, out->rows, inv, pos_of);
+    AIR_CUDA(air_dmalloc((void **)&out->ptr, (size_t)(ns + 1) * sizeof(int64_t)));
+    AIR_CUDA(cudaMallocAsync(&wid, (size_t)ns * sizeof(int32_t), s));
+    block_width_kernel<<<air_counted(grid_cap(ns, 256)), 256, 0, s>>>(m, out->rows, pos_of, nb, wid);
+    AIR_LAUNCH();
+    AIR_TRY(air_exclusive_scan_i32(wid, out->ptr, ns, s));
+    AIR_CUDA(cudaMemcpyAsync(&out->stored, out->ptr + ns, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    AIR_CUDA(cudaStreamSynchronize(s));
+    cudaFreeAsync(wid, s);
+    cudaFreeAsync(inv, s);
+    cudaFreeAsync(pos_of, s);
+    cudaFreeAsync(nb, s);
+    const int64_t cnt = out->stored > 0 ? out->stored : 1;
+    const size_t vb = precision == AIR_PREC_F64 ? 8 : (precision == AIR_PREC_F32 ? 4 : 2);
+    const size_t db = precision == AIR_PREC_F64 ? 8 : 4;
+    AIR_CUDA(air_dmalloc((void **)&out->bc, (size_t)cnt * sizeof(int32_t)));
+    AIR_CUDA(air_dmalloc(&out->v, (size_t)cnt * b * vb));
+    AIR_CUDA(air_dmalloc(&out->dv, (size_t)m * db));
+    unsigned g = grid_cap(ns * 32, 256, 152 * 32);
+    if (precision == AIR_PREC_F64)
+        block_fill_kernel<double, double, false><<<air_counted(g), 256, 0, s>>>(m, out->rows, rp, ci, v, b, out->ptr,
+                                                                                 out->bc, (double *)out->v,
+                                                                                 (double *)out->dv);
+    else if (precision == AIR_PREC_F32)
+        block_fill_kernel<float, float, false><<<air_counted(g), 256, 0, s>>>(m, out->rows, rp, ci, v, b, out->ptr,
+                                                                               out->bc, (float *)out->v,
+                                                                               (float *)out->dv);
+    else
+        block_fill_kernel<__nv_bfloat16, float, true><<<air_counted(g), 256, 0, s>>>(
+            m, out->rows, rp, ci, v, b, out->ptr, out->bc, (__nv_bfloat16 *)out->v, (float *)out->dv);
+    AIR_LAUNCH();
+    return AIR_OK;
+}
+
 int air_sell_spmv_f64(const Sell &S, const double *x, double *y, const double *b, cudaStream_t s) {
+    if (S.b > 0) {
+        BSellArgs<double, double> ba{};
+        ba.m = S.m; ba.ptr = S.ptr; ba.bc = S.bc; ba.v = (const double *)S.v; ba.dv = (const double *)S.dv;
+        ba.rows = S.rows; ba.x = x; ba.y = y; ba.b = b;
+        bsell_launch<double, double, ROW_SPMV>(S.b, ba, s);
+        AIR_LAUNCH();
+        return AIR_OK;
+    }
     SellArgs<double, double> a{};
     a.m = S.m; a.ptr = S.ptr; a.ci = S.ci; a.v = (const double *)S.v; a.rows = S.rows; a.x = x; a.y = y; a.b = b;
     sell_launch<double, double, ROW_SPMV>(a, s);
