@@ -60,7 +60,12 @@ typedef struct {
 typedef struct {
     double theta;        /* classical strength threshold (Section 4: 0.3 for R, 0.2 for C/F) */
     int distance;        /* l-AIR neighbourhood distance (Section 4: 1); 1 or 2 on the GPU */
-    char relax[16];      /* Jacobi sweep pattern over point sets, e.g. "FCF" */
+    char relax[16];      /* relaxation sweeps after the interpolation, one per character: 'F', 'C',
+                            'A' a Jacobi sweep over the F, C or all points ("FCF" by default); 'f',
+                            'c', 'a' a forward Gauss-Seidel sweep (ascending point order, the
+                            values already updated; Section 4 post-relaxes with "fa") over the
+                            same sets, level-scheduled (FP64 and FP32 hierarchies; the many
+                            right-hand-side calls take 'F' and 'C' only) */
     double omega;        /* Jacobi weight */
     int max_coarse;      /* stop coarsening at or below this many rows */
     int max_levels;      /* hard cap on levels (<= 32) */

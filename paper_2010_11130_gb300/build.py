@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libair.so")
-SOURCES = ["scan.cu", "setup_kernels.cu", "first_pass.cu", "adjoint.cu", "batch.cu", "multi_rhs.cu", "solve_kernels.cu", "air_api.cu", "air_noalloc.cu", "hdg_assembly.cu", "falgout.cu"]
+SOURCES = ["scan.cu", "setup_kernels.cu", "first_pass.cu", "adjoint.cu", "batch.cu", "multi_rhs.cu", "solve_kernels.cu", "air_api.cu", "air_noalloc.cu", "hdg_assembly.cu", "falgout.cu", "gauss_seidel.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
 

@@ -80,6 +80,7 @@ void free_level(AirLevel &L) {
     air_free_sell(L.sset[0]);
     air_free_sell(L.sset[1]);
     air_free_sell(L.sr);
+    air_gs_free(L);
     dfree(L.b); dfree(L.x); dfree(L.x2);
 }
 
@@ -405,6 +406,7 @@ int setup_impl(const air_csr *A, const air_options *opt, cudaStream_t s, air_hie
         AIR_TRY(air_cast_d2f(H->cinv, H->cinv32, H->nco * H->nco, s));
     }
     AIR_TRY(air_tune_lanes(H, opt->autotune, s));
+    AIR_TRY(air_gs_build(H, s));
     AIR_CUDA(cudaStreamSynchronize(s));
     return AIR_OK;
 }
@@ -631,8 +633,12 @@ int air_setup(const air_csr *A, double theta, int distance, const air_options *o
     o.theta = theta;
     o.distance = distance;
     o.relax[sizeof(o.relax) - 1] = 0;
-    for (const char *c = o.relax; *c; ++c)
-        if (*c != 'F' && *c != 'C') return AIR_ERR_INVALID_ARG;
+    bool gs = false;
+    for (const char *c = o.relax; *c; ++c) {
+        if (!strchr("FCAfca", *c)) return AIR_ERR_INVALID_ARG;
+        gs = gs || (*c >= 'a');
+    }
+    if (gs && o.precision == AIR_PREC_BF16) return AIR_ERR_UNSUPPORTED;
     if (!(theta >= 0.0) || !(theta <= 1.0) || !(o.theta_r <= 1.0) || o.max_levels < 1 || o.max_levels > AIR_MAX_LEVELS ||
         o.max_dense < 1 || o.restart < 1 || o.restart > 32 || o.max_iter < 0 || o.falgout_block < 0 ||
         (o.falgout_block > 0 && (o.falgout_block % 1024 != 0 || o.falgout_block > 8192)) || o.block_size < 0 ||
@@ -686,14 +692,24 @@ int air_bicgstab_solve(const air_csr *A, const air_hierarchy *H, const double *b
     return st;
 }
 
+namespace {
+bool fc_jacobi_only(const air_hierarchy *H) {
+    for (const char *c = H->opt.relax; *c; ++c)
+        if (*c != 'F' && *c != 'C') return false;
+    return true;
+}
+}  // namespace
+
 int air_vcycle_multi(const air_hierarchy *H, int k, const double *b, double *x, void *stream) {
     if (!H || !b || !x || k < 1 || k > 32) return AIR_ERR_INVALID_ARG;
+    if (!fc_jacobi_only(H)) return AIR_ERR_UNSUPPORTED;
     AirCallStream call((cudaStream_t)stream);
     return air_vcycle_multi_run(H, k, b, x, (cudaStream_t)stream);
 }
 
 int air_vcycle_multi_f32(const air_hierarchy *H, int k, const float *b, float *x, void *stream) {
     if (!H || !b || !x || k < 1 || k > 32) return AIR_ERR_INVALID_ARG;
+    if (!fc_jacobi_only(H)) return AIR_ERR_UNSUPPORTED;
     AirCallStream call((cudaStream_t)stream);
     return air_vcycle_multi_run_f32(H, k, b, x, (cudaStream_t)stream);
 }
@@ -703,6 +719,7 @@ int air_bicgstab_solve_multi(const air_csr *A, const air_hierarchy *H, int k, co
     if (!A || !H || !b || !x || !info || k < 1 || k > 32 || !(rtol > 0.0) || !A->on_device ||
         A->n_rows != H->lev[0].n)
         return AIR_ERR_INVALID_ARG;
+    if (!fc_jacobi_only(H)) return AIR_ERR_UNSUPPORTED;
     AirCallStream call((cudaStream_t)stream);
     return air_bicgstab_multi_impl(H, k, b, x, rtol, (cudaStream_t)stream, info);
 }

@@ -133,6 +133,17 @@ struct AirLevel {
     // lanes per row of the entry-form kernels: F sweep, C sweep, restriction
     // (1: one thread per row; more: the row's entries split over that many lanes)
     int lanes[3] = {1, 1, 1};
+    // forward Gauss-Seidel level schedules of the F points, the C points and
+    // all points: rows grouped by their depth in the graph of lower-index
+    // couplings (dev_rows, device), group k = dev_rows[ptr[k] .. ptr[k+1])
+    // with ptr on the host
+    struct GsSchedule {
+        int64_t m = 0;
+        int32_t depth = 0;
+        int32_t *dev_rows = nullptr;
+        int64_t *ptr = nullptr;      // host, depth + 1
+    } gs[3];
+    float *v32 = nullptr;            // FP32 copy of A_l's values (Gauss-Seidel on an FP32 hierarchy)
     // V-cycle work vectors (precision of the hierarchy)
     void *b = nullptr, *x = nullptr, *x2 = nullptr;
 };
@@ -237,6 +248,14 @@ int air_vcycle_multi_run_f32(const air_hierarchy *H, int k, const float *b, floa
 int air_bicgstab_multi_impl(const air_hierarchy *H, int k, const double *b, double *x, double rtol,
                             cudaStream_t s, air_solve_info *info);
 void air_free_multi(air_hierarchy *H);
+
+// gauss_seidel.cu: level schedules of the forward Gauss-Seidel sweeps the
+// relaxation string asks for ('f', 'c', 'a'), built at the end of setup, and
+// one sweep x <- GS(x) over set which (0 F, 1 C, 2 all); xn is n scratch
+int air_gs_build(air_hierarchy *H, cudaStream_t s);
+void air_gs_free(AirLevel &L);
+template <typename T>
+int air_gs_sweep(const AirLevel &L, int which, T omega, const T *b, T *x, T *xn, cudaStream_t s);
 
 // solve_kernels.cu
 // y = A x, or y = b - A x if b != NULL; nnz < 0 / maxrow <= 0 when unknown

@@ -686,7 +686,7 @@ void spmv_dispatch(int64_t n, int64_t nnz, int32_t maxrow, const int64_t *rp, co
 // new values of the set's rows go to tmp, then are scattered back.
 template <typename TV, typename T>
 void jacobi_dispatch(const AirLevel &L, const T *diag, const T *dinv, int which, T omega, const T *b, T *x, T *tmp,
-                     cudaStream_t s) {
+                     cudaStream_t s, bool scatter = true) {
     const Sell &S = L.sset[which];
     if (S.m == 0) return;
     if (S.b > 0) {
@@ -694,14 +694,29 @@ void jacobi_dispatch(const AirLevel &L, const T *diag, const T *dinv, int which,
         ba.m = S.m; ba.ptr = S.ptr; ba.bc = S.bc; ba.v = (const TV *)S.v; ba.dv = (const T *)S.dv; ba.rows = S.rows;
         ba.x = x; ba.y = tmp; ba.b = b; ba.dinv = dinv; ba.omega = omega;
         bsell_launch<TV, T, ROW_JACOBI>(S.b, ba, s);
-        scatter_kernel<T><<<air_counted(grid_cap(S.m, 256)), 256, 0, s>>>(S.m, S.rows, tmp, x);
+        if (scatter) scatter_kernel<T><<<air_counted(grid_cap(S.m, 256)), 256, 0, s>>>(S.m, S.rows, tmp, x);
         return;
     }
     SellArgs<TV, T> a{};
     a.m = S.m; a.ptr = S.ptr; a.ci = S.ci; a.v = (const TV *)S.v; a.rows = S.rows;
     a.x = x; a.y = tmp; a.b = b; a.dinv = dinv; a.diag = diag; a.omega = omega;
     sell_launch<TV, T, ROW_JACOBI>(a, s, L.lanes[which]);
-    scatter_kernel<T><<<air_counted(grid_cap(S.m, 256)), 256, 0, s>>>(S.m, S.rows, tmp, x);
+    if (scatter) scatter_kernel<T><<<air_counted(grid_cap(S.m, 256)), 256, 0, s>>>(S.m, S.rows, tmp, x);
+}
+
+// One Jacobi sweep over all points: both point sets from the same old x into
+// the two halves of tmp, then both scatters.
+template <typename TV, typename T>
+void jacobi_all_dispatch(const AirLevel &L, const T *diag, const T *dinv, T omega, const T *b, T *x, T *tmp,
+                         cudaStream_t s) {
+    T *tf = tmp, *tc = tmp + L.sset[0].m;
+    jacobi_dispatch<TV, T>(L, diag, dinv, 0, omega, b, x, tf, s, false);
+    jacobi_dispatch<TV, T>(L, diag, dinv, 1, omega, b, x, tc, s, false);
+    for (int w = 0; w < 2; ++w) {
+        const Sell &S = L.sset[w];
+        if (S.m > 0)
+            scatter_kernel<T><<<air_counted(grid_cap(S.m, 256)), 256, 0, s>>>(S.m, S.rows, w == 0 ? tf : tc, x);
+    }
 }
 
 // The separate FP32 diagonal (BF16 storage only) and 1/a_ii in the vector
@@ -750,8 +765,14 @@ int vcycle_t(const air_hierarchy *H, const T *b0, T *x0, cudaStream_t s) {
         const T *diag = (const T *)lvl_diag<TV>(A);
         const T *dinv = lvl_dinv<T>(A);
         for (int q = 0; q < ns; ++q) {
-            int which = relax[q] == 'C' ? 1 : 0;
-            jacobi_dispatch<TV, T>(A, diag, dinv, which, omega, bl, out, alt, s);
+            const char c = relax[q];
+            if (c == 'F' || c == 'C') {
+                jacobi_dispatch<TV, T>(A, diag, dinv, c == 'C' ? 1 : 0, omega, bl, out, alt, s);
+            } else if (c == 'A') {
+                jacobi_all_dispatch<TV, T>(A, diag, dinv, omega, bl, out, alt, s);
+            } else {                                   // 'f', 'c', 'a': forward Gauss-Seidel
+                AIR_TRY(air_gs_sweep<T>(A, c == 'f' ? 0 : (c == 'c' ? 1 : 2), omega, bl, out, alt, s));
+            }
         }
     }
     AIR_LAUNCH();
