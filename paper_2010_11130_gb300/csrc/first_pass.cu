@@ -200,6 +200,13 @@ __device__ __forceinline__ unsigned lanemask_lt() {
     return m;
 }
 
+// Measures are read through L1: only this warp writes them, with plain
+// stores that the same SM's L1 sees, and a __syncwarp orders every pick's
+// stores before the next pick's loads.
+__device__ __forceinline__ int lam_load(const int8_t *p) {
+    return (int)__ldca((const signed char *)p);
+}
+
 __device__ __forceinline__ void prefetch_block(const uint32_t *p) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "r"(BLK_W * 4u)
                  : "memory");
@@ -332,15 +339,11 @@ __global__ void __launch_bounds__(32) rs5_warp_kernel(RS5Args a) {
         const int32_t lbase = s.cl[B] * 512;
         const int32_t i = lbase + sw * 32 + (__ffs(word) - 1);
         if (++picks > (unsigned long long)a.n || i >= a.n) { failed = true; break; }
-        // the next members of the same line are the likely next picks: warm their blocks in L2
+        // the next member of the same line is the likely next pick
         int32_t nxt = -1;
         {
             const uint32_t rest = lane == sw ? (word & (word - 1u)) : wv;
             const unsigned nz = __ballot_sync(FULL, rest != 0u);
-            if (rest != 0u && __popc(nz & lanemask_lt()) < 3) {
-                const int32_t q = lbase + lane * 32 + (__ffs(rest) - 1);
-                if (q < a.n) prefetch_block(a.blocks + (size_t)q * BLK_W);
-            }
             if (nz) {
                 const int fl = __ffs(nz) - 1;
                 const uint32_t rw = __shfl_sync(FULL, rest, fl);
@@ -379,8 +382,8 @@ __global__ void __launch_bounds__(32) rs5_warp_kernel(RS5Args a) {
 
         // ---- round trip 2: measures of the listed points
         const int32_t k0 = (int32_t)(e0 & K_MASK), k1 = (int32_t)(e1 & K_MASK);
-        const int l0 = (lane >= 1 && lane < np) ? (int)__ldcg(a.lam + k0) : -3;
-        const int l1 = (two && lane + 32 < np) ? (int)__ldcg(a.lam + k1) : -3;
+        const int l0 = (lane >= 1 && lane < np) ? lam_load(a.lam + k0) : -3;
+        const int l1 = (two && lane + 32 < np) ? lam_load(a.lam + k1) : -3;
         // F_new: the undecided members of S^T_i, bit t for entry t
         const unsigned f0 = __ballot_sync(FULL, lane >= 1 && lane <= nj && l0 >= 0);
         const unsigned f1 = __ballot_sync(FULL, lane + 32 <= nj && l1 >= 0);
@@ -439,7 +442,7 @@ __global__ void __launch_bounds__(32) rs5_warp_kernel(RS5Args a) {
                     const uint32_t e = __ldcg(a.ovf + op + (p - BLK_E));
                     const uint64_t m = __ldcg((const unsigned long long *)a.ovfm + op + (p - BLK_E));
                     k = (int32_t)(e & K_MASK);
-                    const int l = (int)__ldcg(a.lam + k);
+                    const int l = lam_load(a.lam + k);
                     settle(k, l, change(e, m, l, false), ob, nbk);   // S^T_i has at most 62 members
                 }
                 const bool has = ob != 0 || nbk != 0;
@@ -461,16 +464,6 @@ __global__ void __launch_bounds__(32) rs5_warp_kernel(RS5Args a) {
             if (two) fn(rk1, ob1, nb1);
             for (int q = lane; q < nx; q += 32) fn(s.rk[q], (int)s.rob[q], (int)s.rnb[q]);
         };
-        // one population change per bucket and register round, from warp matching
-        // (lanes without a change share one key: match cost grows with the
-        // number of distinct keys).  Returns the population before the change
-        // to the group's leader.
-        auto add_pop = [&](int b, int sign) {
-            const unsigned m = __match_any_sync(FULL, (uint32_t)b);
-            int old = -1;
-            if (b && lane == __ffs(m) - 1) old = atomicAdd(&s.pop[b], sign * __popc(m));
-            return old + (b && lane == __ffs(m) - 1 ? sign * __popc(m) : 0);
-        };
         // populations and cursors.  A change inside a bucket's cursor line
         // toggles its bit (a removal clears a set bit, an insertion sets a clear
         // one); an insertion below the cursor only lowers the pending line, which
@@ -479,8 +472,8 @@ __global__ void __launch_bounds__(32) rs5_warp_kernel(RS5Args a) {
         // insertions below it.  A: removals
         {
             auto forget = [&](int b) { s.cl[b] = CL_INF; s.pl[b] = CL_INF; };
-            if (add_pop(ob0, -1) == 0) forget(ob0);
-            if (two && add_pop(ob1, -1) == 0) forget(ob1);
+            if (ob0 && atomicSub(&s.pop[ob0], 1) == 1) forget(ob0);
+            if (two && ob1 && atomicSub(&s.pop[ob1], 1) == 1) forget(ob1);
             for (int q = lane; q < nx; q += 32) {
                 const int ob = s.rob[q];
                 if (ob && atomicSub(&s.pop[ob], 1) == 1) forget(ob);
@@ -491,8 +484,8 @@ __global__ void __launch_bounds__(32) rs5_warp_kernel(RS5Args a) {
         });
         __syncwarp();
         // B: insertions
-        add_pop(nb0, 1);
-        if (two) add_pop(nb1, 1);
+        if (nb0) atomicAdd(&s.pop[nb0], 1);
+        if (two && nb1) atomicAdd(&s.pop[nb1], 1);
         for (int q = lane; q < nx; q += 32)
             if (s.rnb[q]) atomicAdd(&s.pop[s.rnb[q]], 1);
         each([&](int32_t k, int, int nbk) {
