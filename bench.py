@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--distance", type=int, default=1, help="l-AIR neighbourhood distance (1 or 2)")
     ap.add_argument("--no-gpu-assembly", action="store_true")
     ap.add_argument("--no-gs", action="store_true", help="skip the forward Gauss-Seidel variant")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched independent-problems leg")
     ap.add_argument("--autotune", type=int, default=1, help="time the lanes per row of every level at setup")
     ap.add_argument("--block-size", type=int, default=-1,
                     help="block form of the finest operator: facet block size b (-1: b of the workload, 0: off)")
@@ -573,6 +574,10 @@ def run_ours(args):
     if not args.no_gpu_assembly:
         gpu_asm = gpu_assembly_leg(args, s, stream)
         gpu_asm["host_s"] = gen_s
+    batched = None
+    if not args.no_batched:
+        batched = batched_leg(args)
+        batched["workload"] = f"batched_{args.batch_count}_st2d_n{args.batch_nmin}-{args.batch_nmax}"
         torch.cuda.empty_cache()
 
     # end to end through the C ABI with pinned host buffers
@@ -634,7 +639,8 @@ def run_ours(args):
                                             "vcycle_gbs": rl["bf16"]["gbs"], "warmup": w_o, "steps": k_o},
             "solve_stage_s": {k: breakdown[k]["solve_s"] for k in breakdown},
             "falgout_split_f32_precond": falgout,
-            "gauss_seidel_fa_f32_precond": gs},
+            "gauss_seidel_fa_f32_precond": gs,
+            "batched_independent_problems": batched},
         "roofline": {"bound": "hbm", "kernel": "V-cycle (FP32 hierarchy, all levels)",
                      "achieved": v32["gbs"], "peak": gbs_peak, "unit": "GB/s",
                      "frac": v32["gbs"] / gbs_peak, "traffic": vcycle_traffic(v32["bytes"]),
@@ -658,54 +664,100 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def run_batched(args):
-    """Independent uneven problems (seeded recipe of sthdg.problems.batched_problems):
-    FP32 hierarchies built with air_setup_batch and solved with
-    air_gmres_solve_batch, against the same calls made one problem at a time."""
+def gpu_system(prob):
+    """The trace system of a problem assembled, condensed and block-scaled on
+    the GPU (air_hdg_assemble): (device CSR, device right-hand side)."""
+    import torch
+    from paper_2010_11130_gb300 import hdg
+    from sthdg.mesh import build_mesh
+    mesh = build_mesh(prob.D, prob.n, reflect=prob.reflect, lower=prob.lower, upper=prob.upper,
+                      vertex_map=prob.vertex_map)
+    tab = hdg.HdgTables(prob.D, prob.p)
+    hm = hdg.HdgMesh.from_mesh(mesh)
+    xv, xf, xF = hdg.points(hm, tab)
+    xv, xf, xF = xv.cpu().numpy(), xf.cpu().numpy(), xF.cpu().numpy()
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+    data = hdg.HdgData(prob.nu, 10.0 * prob.p ** 2, dev(prob.velocity(xv)), dev(prob.velocity(xf)),
+                       dev(prob.source(xv)), dev(prob.u_initial(xf)), dev(prob.g_dirichlet(xF)))
+    sysg = hdg.assemble(hm, tab, data)
+    return sysg.A, sysg.rhs
+
+
+def batched_leg(args):
+    """Independent uneven problems (seeded recipe of sthdg.problems.batched_problems,
+    assembled on the GPU): FP32 hierarchies built with air_setup_batch (level by
+    level, each level's local l-AIR solves of all problems in one launch) and
+    solved with air_gmres_solve_batch (lockstep rounds, the V-cycles of a round in
+    one CUDA graph), against the same calls made one problem at a time.  Parity
+    per problem: the batched solution equals the single-problem solution bit for
+    bit, with the same iteration count."""
     import torch
     import paper_2010_11130_gb300 as air
-    from sthdg import assemble
     from sthdg.problems import batched_problems
-    air.build()
     t0 = time.perf_counter()
     probs, _ = batched_problems(args.batch_count, (args.batch_nmin, args.batch_nmax))
-    sys_ = [assemble(p, workers=args.workers) for p in probs]
+    systems = [gpu_system(p) for p in probs]
+    torch.cuda.synchronize()
     gen_s = time.perf_counter() - t0
-    As = [air.CSR.from_host(s.row_ptr, s.col, s.val) for s in sys_]
-    bs = [torch.from_numpy(np.ascontiguousarray(s.rhs)).cuda() for s in sys_]
-    air.setup(As[0], precision=1)                     # warm-up: module load, memory pools
+    As = [A for A, _ in systems]
+    bs = [b for _, b in systems]
+    air.setup(As[int(np.argmin([A.n for A in As]))], precision=1)   # warm-up: module load, memory pools
     torch.cuda.synchronize()
 
-    def batch_step():
-        Hs, st = air.setup_batch(As, precision=1)
-        assert all(x == 0 for x in st), st
-        xs, infos, st2 = air.gmres_solve_batch(As, Hs, bs, rtol=args.rtol)
-        assert all(x == 0 for x in st2), st2
-        return infos
-
-    def serial_step():
-        infos = []
-        for A, b in zip(As, bs):
-            H = air.setup(A, precision=1)
-            infos.append(air.gmres_solve(A, H, b, rtol=args.rtol)[1])
-        return infos
-
-    times = {}
-    for name, fn in (("batched", batch_step), ("one_at_a_time", serial_step)):
+    def clock(fn):
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        infos = fn()
+        t = time.perf_counter()
+        r = fn()
         torch.cuda.synchronize()
-        times[name] = time.perf_counter() - t0
+        return r, time.perf_counter() - t
+
+    l0 = air.kernel_launches()
+    (Hs, st), ts_b = clock(lambda: air.setup_batch(As, precision=1))
+    assert all(x == 0 for x in st), st
+    l1 = air.kernel_launches()
+    (xs, infos, st2), tv_b = clock(lambda: air.gmres_solve_batch(As, Hs, bs, rtol=args.rtol))
+    assert all(x == 0 for x in st2), st2
+    l2 = air.kernel_launches()
+    del Hs
+    ts_1 = tv_1 = 0.0
+    parity = []
+    per = []
+    launches_1 = [0, 0]
+    for A, b, x, inf in zip(As, bs, xs, infos):
+        a0 = air.kernel_launches()
+        H, t_s = clock(lambda: air.setup(A, precision=1))
+        a1 = air.kernel_launches()
+        (x1, inf1), t_v = clock(lambda: air.gmres_solve(A, H, b, rtol=args.rtol))
+        a2 = air.kernel_launches()
+        launches_1[0] += a1 - a0
+        launches_1[1] += a2 - a1
+        ts_1 += t_s
+        tv_1 += t_v
+        per.append([round(t_s, 4), round(t_v, 4)])
+        parity.append(bool(torch.equal(x, x1)) and inf.iters == inf1.iters)
+        del H
+    return {"s": ts_b + tv_b, "setup_s": ts_b, "solve_s": tv_b,
+            "one_at_a_time_s": ts_1 + tv_1, "one_at_a_time_setup_s": ts_1, "one_at_a_time_solve_s": tv_1,
+            "speedup": (ts_1 + tv_1) / (ts_b + tv_b),
+            "iters": [int(i.iters) for i in infos], "parity_per_problem_bit_exact": parity,
+            "one_at_a_time_per_problem_setup_solve_s": per,
+            "launches": {"batched_setup": l1 - l0, "batched_solve": l2 - l1,
+                         "one_at_a_time_setup": launches_1[0], "one_at_a_time_solve": launches_1[1]},
+            "problems": [{"n": p.n, "p": p.p, "nu": p.nu, "unknowns": int(A.n)} for p, A in zip(probs, As)],
+            "unknowns_total": int(sum(A.n for A in As)), "generate_s": gen_s,
+            "timing": "wall clock around each call with device synchronisation, data resident"}
+
+
+def run_batched(args):
+    """The batched leg alone, as its own JSON line."""
+    import paper_2010_11130_gb300 as air
+    air.build()
+    r = batched_leg(args)
     out = {"metric": "batched AIR-GMRES time-to-1e-8 over independent problems (setup+solve s)",
-           "value": times["batched"], "unit": "s", "n_gpus": 1, "steps": 1, "warmup": 1,
+           "value": r["s"], "unit": "s", "n_gpus": 1, "steps": 1, "warmup": 1,
            "higher_is_better": False, "dtype": "f32 hierarchy / f64 Krylov", "data": "synthetic",
-           "config": {"workload": f"batched_{args.batch_count}_st2d_n{args.batch_nmin}-{args.batch_nmax}",
-                      "problems": [{"n": p.n, "p": p.p, "nu": p.nu, "unknowns": s.n} for p, s in zip(probs, sys_)],
-                      "unknowns_total": int(sum(s.n for s in sys_))},
-           "one_at_a_time_s": times["one_at_a_time"],
-           "speedup": times["one_at_a_time"] / times["batched"],
-           "iters": [i.iters for i in infos], "generate_s": gen_s}
+           "config": {"workload": f"batched_{args.batch_count}_st2d_n{args.batch_nmin}-{args.batch_nmax}"},
+           **r}
     print(json.dumps(out))
 
 

@@ -194,16 +194,35 @@ int air_bicgstab_solve_multi(const air_csr *A, const air_hierarchy *H, int k, co
                              double rtol, void *stream, air_solve_info *info);
 
 /* Independent problems at once.  The paper solves one system at a time;
- * these run count independent setups (or solves) concurrently, one host
- * thread and one stream per problem (streams[k], or a library-created stream
- * when streams is NULL or streams[k] is NULL), and return when all are done.
- * Each problem's result is exactly that of the single-problem call.  A is an
- * array of count air_csr; out / H / b / x / info / status are arrays of
- * count.  status[k] (if status is not NULL) receives problem k's status; the
- * return value is the first negative status, else AIR_OK (a solve that stops
- * at max_iter reports AIR_NOT_CONVERGED in status[k] and info[k] only).  A
- * hierarchy may appear only once in a solve batch (AIR_ERR_INVALID_ARG):
- * its Krylov workspace serves one solve at a time. */
+ * these run count independent setups (or solves) together and return when
+ * all are done.  Each problem works on its own stream (streams[k], or a
+ * library-created stream when streams is NULL or streams[k] is NULL).
+ *
+ * air_setup_batch builds the hierarchies level by level in lockstep: every
+ * problem's strength, transpose and C/F splitting of level l run on its own
+ * host thread and stream (the one-warp first passes of different problems
+ * run side by side), then the local l-AIR solves of level l of all problems
+ * run as one kernel launch over the union of their C points (Section 3), then
+ * each problem builds P and A_{l+1}.  theta, distance and opt apply to every
+ * problem.
+ *
+ * air_gmres_solve_batch runs every problem's flexible GMRES(m) in lockstep
+ * rounds on one host thread: in each round the V-cycles of all problems in an
+ * Arnoldi step are one CUDA graph launch (a gather of the vectors into the
+ * hierarchies, their V-cycles as parallel branches, a scatter back; the
+ * graph is rebuilt only when a problem finishes), then each problem's
+ * matrix product, CGS2 and Givens update run on its stream, with one host
+ * synchronisation per round for all problems.  Hierarchies of different
+ * precisions may be mixed.
+ *
+ * Each problem's result is exactly that of the single-problem call (the same
+ * kernels on the same data).  A is an array of count air_csr; out / H / b / x
+ * / info / status are arrays of count.  status[k] (if status is not NULL)
+ * receives problem k's status; the return value is the first negative
+ * status, else AIR_OK (a solve that stops at max_iter reports
+ * AIR_NOT_CONVERGED in status[k] and info[k] only).  A hierarchy may appear
+ * only once in a solve batch (AIR_ERR_INVALID_ARG): its Krylov workspace
+ * serves one solve at a time. */
 int air_setup_batch(int count, const air_csr *A, double theta, int distance, const air_options *opt,
                     void *const *streams, air_hierarchy **out, int *status);
 int air_gmres_solve_batch(int count, const air_csr *A, const air_hierarchy *const *H, const double *const *b,

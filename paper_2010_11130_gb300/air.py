@@ -494,7 +494,8 @@ class AdjointSolver:
 
 # ------------------------------------------------------------------ batches
 def setup_batch(As, theta: float = 0.25, distance: int = 1, streams=None, **opts):
-    """air_setup_batch: independent setups at once (one host thread and stream each).
+    """air_setup_batch: independent setups at once, level by level, with each
+    level's local l-AIR solves of all problems in one launch.
 
     Returns (hierarchies, statuses); a failed problem has hierarchy None.
     """
@@ -510,7 +511,8 @@ def setup_batch(As, theta: float = 0.25, distance: int = 1, streams=None, **opts
 
 
 def gmres_solve_batch(As, Hs, bs, xs=None, rtol: float = 1e-8, streams=None):
-    """air_gmres_solve_batch: independent device solves at once.  Returns (xs, infos, statuses)."""
+    """air_gmres_solve_batch: independent device solves in lockstep, the V-cycles of
+    each round in one CUDA graph.  Returns (xs, infos, statuses)."""
     import torch
     k = len(As)
     if xs is None:

@@ -139,22 +139,26 @@ struct PhaseTimer {
     }
 };
 
-// Build level l+1 from level l.  Returns AIR_OK with *stop = 1 when level l
-// is the coarsest.
-int coarsen(air_hierarchy *H, int l, cudaStream_t s, int *stop) {
+}  // namespace
+
+// First half of building level l+1 from level l: strength, transpose, C/F
+// splitting, coarse ids, the l-AIR neighbourhood sizes and R's arrays.  Sets
+// c->stop = 1 (and keeps nothing) when level l is the coarsest; otherwise the
+// local l-AIR solves of c->LS are ready to run.
+int air_coarsen_split(air_hierarchy *H, int l, cudaStream_t s, AirCoarsen *c) {
     AirLevel &L = H->lev[l];
     const air_options &o = H->opt;
     int64_t n = L.n;
-    *stop = 0;
+    *c = AirCoarsen{};
     PhaseTimer T(H, s);
     T.start(0);
     // a1 strength
-    int32_t *cnt = nullptr;
+    int32_t *&cnt = c->cnt;
     AIR_TRY(dalloc(&cnt, n + 1));
     AIR_TRY(dalloc(&L.srp, n + 1));
     AIR_TRY(air_strength(L, o.theta, nullptr, nullptr, cnt, 0, s));
     AIR_TRY(air_exclusive_scan_i32(cnt, L.srp, n, s));
-    int32_t *dmax = nullptr;
+    int32_t *&dmax = c->dmax;
     AIR_TRY(dalloc(&dmax, 1));
     AIR_CUDA(cudaMemsetAsync(dmax, 0, sizeof(int32_t), s));
     AIR_TRY(air_reduce_max_i32(cnt, n, dmax, s));
@@ -187,7 +191,7 @@ int coarsen(air_hierarchy *H, int l, cudaStream_t s, int *stop) {
     AIR_TRY(check_err(H, s));
     dfree(strp);
     dfree(stci);
-    int64_t *scanw = nullptr;
+    int64_t *&scanw = c->scanw;
     AIR_TRY(dalloc(&scanw, n + 1));
     AIR_TRY(dalloc(&L.cid, n));
     int64_t nc = 0;
@@ -196,7 +200,8 @@ int coarsen(air_hierarchy *H, int l, cudaStream_t s, int *stop) {
         dfree(cnt); dfree(dmax); dfree(scanw);
         dfree(L.srp); dfree(L.sci); dfree(L.cf); dfree(L.cid);
         L.nnz_s = 0;
-        *stop = 1;
+        *c = AirCoarsen{};
+        c->stop = 1;
         return AIR_OK;
     }
     L.nc = nc;
@@ -207,8 +212,8 @@ int coarsen(air_hierarchy *H, int l, cudaStream_t s, int *stop) {
     AIR_TRY(air_point_list(n, L.cf, 0, L.frows, scanw, s));
     // a4 l-AIR restriction, from its own strength graph when its threshold differs
     T.start(3);
-    int64_t *rsrp = nullptr;
-    int32_t *rsci = nullptr;
+    int64_t *&rsrp = c->rsrp;
+    int32_t *&rsci = c->rsci;
     if (o.theta_r >= 0.0 && o.theta_r != o.theta) {
         AIR_TRY(dalloc(&rsrp, n + 1));
         AIR_TRY(air_strength(L, o.theta_r, nullptr, nullptr, cnt, 0, s));
@@ -231,19 +236,33 @@ int coarsen(air_hierarchy *H, int l, cudaStream_t s, int *stop) {
     L.max_m = max_m1 - 1;
     AIR_TRY(dalloc(&L.rci, L.nnz_r));
     AIR_TRY(dalloc(&L.rv, L.nnz_r));
-    int64_t *dsing = nullptr;
-    AIR_TRY(dalloc(&dsing, 1));
-    AIR_CUDA(cudaMemsetAsync(dsing, 0, sizeof(int64_t), s));
-    AirLevel LS = L;            // the level with R's strength graph in place of the coarsening one
+    AIR_TRY(dalloc(&c->dsing, 1));
+    AIR_CUDA(cudaMemsetAsync(c->dsing, 0, sizeof(int64_t), s));
+    c->LS = L;                  // the level with R's strength graph in place of the coarsening one
     if (rsrp) {
-        LS.srp = rsrp;
-        LS.sci = rsci;
+        c->LS.srp = rsrp;
+        c->LS.sci = rsci;
     }
-    AIR_TRY(air_lair_solve(LS, L.max_m, o.distance, dsing, s));
-    AIR_TRY(read_i64(dsing, &L.n_singular, s));
-    dfree(dsing);
-    dfree(rsrp);
-    dfree(rsci);
+    AIR_CUDA(cudaStreamSynchronize(s));
+    return AIR_OK;
+}
+
+// Second half, after the local l-AIR solves of c->LS have run: the count of
+// singular local systems, one-point P and the Galerkin product A_{l+1}.
+int air_coarsen_finish(air_hierarchy *H, int l, cudaStream_t s, AirCoarsen *c) {
+    AirLevel &L = H->lev[l];
+    const air_options &o = H->opt;
+    const int64_t n = L.n, nc = L.nc;
+    int32_t *cnt = c->cnt, *dmax = c->dmax;
+    int64_t *scanw = c->scanw;
+    PhaseTimer T(H, s);
+    AIR_TRY(read_i64(c->dsing, &L.n_singular, s));
+    dfree(c->dsing);
+    dfree(c->rsrp);
+    dfree(c->rsci);
+    c->dsing = nullptr;
+    c->rsrp = nullptr;
+    c->rsci = nullptr;
     // a5 one-point interpolation
     T.start(4);
     AIR_TRY(dalloc(&L.pcol, n));
@@ -276,11 +295,39 @@ int coarsen(air_hierarchy *H, int l, cudaStream_t s, int *stop) {
     C.ci = acci;
     C.v = acv;
     dfree(cnt); dfree(dmax); dfree(scanw);
+    *c = AirCoarsen{};
     AIR_CUDA(cudaStreamSynchronize(s));
     return AIR_OK;
 }
 
-int setup_impl(const air_csr *A, const air_options *opt, cudaStream_t s, air_hierarchy *H) {
+// The local l-AIR solves of one level, timed as the l-AIR phase.
+int air_coarsen_lair(air_hierarchy *H, int l, cudaStream_t s, AirCoarsen *c) {
+    PhaseTimer T(H, s);
+    T.start(3);
+    return air_lair_solve(c->LS, H->lev[l].max_m, H->opt.distance, c->dsing, s);
+}
+
+// Adds a batched launch's time to a hierarchy's l-AIR phase.
+void air_add_phase_ms(air_hierarchy *H, int phase, double ms) { H->phase_ms[phase] += ms; }
+
+namespace {
+
+// Build level l+1 from level l.  Returns AIR_OK with *stop = 1 when level l
+// is the coarsest.
+int coarsen(air_hierarchy *H, int l, cudaStream_t s, int *stop) {
+    AirCoarsen c;
+    AIR_TRY(air_coarsen_split(H, l, s, &c));
+    *stop = c.stop;
+    if (c.stop) return AIR_OK;
+    AIR_TRY(air_coarsen_lair(H, l, s, &c));
+    return air_coarsen_finish(H, l, s, &c);
+}
+
+}  // namespace
+
+// Level 0 of a new hierarchy: options, the finest operator (borrowed when it
+// is on the device and FP64), validation.
+int air_setup_begin(const air_csr *A, const air_options *opt, cudaStream_t s, air_hierarchy *H) {
     H->opt = *opt;
     AIR_CUDA(cudaGetDevice(&H->dev));
     AIR_TRY(dalloc(&H->d_err, 1));
@@ -312,15 +359,19 @@ int setup_impl(const air_csr *A, const air_options *opt, cudaStream_t s, air_hie
         AIR_TRY(air_validate_csr(L0.n, L0.nnz, L0.rp, L0.ci, L0.v, H->d_err, s));
         AIR_TRY(check_err(H, s));
     }
-    int l = 0;
-    for (;;) {
-        H->nlev = l + 1;
-        if (H->lev[l].n <= opt->max_coarse || l == opt->max_levels - 1) break;
-        int stop = 0;
-        AIR_TRY(coarsen(H, l, s, &stop));
-        if (stop) break;
-        ++l;
-    }
+    H->nlev = 1;
+    return AIR_OK;
+}
+
+// True when level l (the last built) is to be the coarsest without trying to coarsen it.
+bool air_setup_is_coarsest(const air_hierarchy *H, int l) {
+    return H->lev[l].n <= H->opt.max_coarse || l == H->opt.max_levels - 1;
+}
+
+// Everything after the last level: coarsest inverse, smoother diagonals,
+// precision copies, the FP64 copy of A for GMRES, tuning and schedules.
+int air_setup_end(air_hierarchy *H, cudaStream_t s) {
+    const air_options *opt = &H->opt;
     // coarsest level: dense inverse
     AirLevel &Lc = H->lev[H->nlev - 1];
     H->nco = Lc.n;
@@ -411,6 +462,22 @@ int setup_impl(const air_csr *A, const air_options *opt, cudaStream_t s, air_hie
     return AIR_OK;
 }
 
+namespace {
+
+int setup_impl(const air_csr *A, const air_options *opt, cudaStream_t s, air_hierarchy *H) {
+    AIR_TRY(air_setup_begin(A, opt, s, H));
+    int l = 0;
+    for (;;) {
+        H->nlev = l + 1;
+        if (air_setup_is_coarsest(H, l)) break;
+        int stop = 0;
+        AIR_TRY(coarsen(H, l, s, &stop));
+        if (stop) break;
+        ++l;
+    }
+    return air_setup_end(H, s);
+}
+
 int ensure_workspace(air_hierarchy *H, int64_t n, int m) {
     if (H->ws_n == n && H->ws_m >= m) return AIR_OK;
     free_workspace(H);
@@ -438,72 +505,153 @@ int norm2(int64_t n, const double *v, double *partials, int nblk, double *dst, c
     return AIR_OK;
 }
 
-int gmres_impl(const AirLevel &A0, const air_hierarchy *Hc, const double *b, double *x, double rtol,
-               cudaStream_t s, air_solve_info *info) {
-    air_hierarchy *H = const_cast<air_hierarchy *>(Hc);
-    const int64_t n = A0.n;
-    const int m = H->opt.restart;
-    AIR_TRY(ensure_workspace(H, n, m));
-    const int nblk = air_reduce_nblk(n);
-    double *h1 = H->hcol, *h2 = H->hcol + (m + 2);
-    double *sc = H->scal;   // [0] ||b||^2, [1] estimate, [2] h_{j+1,j}, [3] ||r||^2
+}  // namespace
+
+// Flexible GMRES(m) with classical Gram-Schmidt applied twice and Givens
+// rotations on the device (Section 5.1), split at its host reads so that
+// independent problems can step in lockstep (batch.cu).  Every phase enqueues
+// its work on g.s and ends with a device-to-host copy; the matching air_gmres_after_*
+// runs once the stream has been synchronised and decides the next phase.
+int air_gmres_open(AirGmres &g, const AirLevel &A0, const air_hierarchy *Hc, const double *b, double *x,
+                   double rtol, cudaStream_t s, air_solve_info *info) {
+    g.H = const_cast<air_hierarchy *>(Hc);
+    g.A0 = &A0;
+    g.b = b;
+    g.x = x;
+    g.rtol = rtol;
+    g.s = s;
+    g.info = info;
+    g.n = A0.n;
+    g.m = g.H->opt.restart;
+    AIR_TRY(ensure_workspace(g.H, g.n, g.m));
+    g.nblk = air_reduce_nblk(g.n);
+    g.it = 0;
+    g.j = 0;
+    g.k = 0;
     info->iters = 0;
     info->restarts = 0;
     info->vcycles = 0;
     info->relres = 0.0;
     info->status = AIR_NOT_CONVERGED;
-    AIR_TRY(air_fill_zero(x, n, s));
-    AIR_TRY(norm2(n, b, H->partials, nblk, sc, s));
-    AIR_CUDA(cudaMemcpyAsync(H->h_est, sc, sizeof(double), cudaMemcpyDeviceToHost, s));
-    AIR_CUDA(cudaStreamSynchronize(s));
-    double bnorm = sqrt(H->h_est[0]);
-    if (bnorm == 0.0) {
-        info->status = AIR_OK;
+    double *sc = g.H->scal;   // [0] ||b||^2, [1] estimate, [2] h_{j+1,j}, [3] ||r||^2
+    AIR_TRY(air_fill_zero(x, g.n, s));
+    AIR_TRY(norm2(g.n, b, g.H->partials, g.nblk, sc, s));
+    AIR_CUDA(cudaMemcpyAsync(g.H->h_est, sc, sizeof(double), cudaMemcpyDeviceToHost, s));
+    g.phase = AirGmres::OPENED;
+    return AIR_OK;
+}
+
+void air_gmres_after_open(AirGmres &g) {
+    g.bnorm = sqrt(g.H->h_est[0]);
+    if (g.bnorm == 0.0) {
+        g.info->status = AIR_OK;
+        g.phase = AirGmres::DONE;
+    } else {
+        g.phase = AirGmres::CYCLE;
+    }
+}
+
+// Start of a restart cycle: r = b - A x into V_0 and its norm.
+int air_gmres_cycle(AirGmres &g) {
+    air_hierarchy *H = g.H;
+    AIR_TRY(air_sell_spmv_f64(H->a0, g.x, H->V, g.b, g.s));
+    AIR_TRY(norm2(g.n, H->V, H->partials, g.nblk, H->scal + 3, g.s));
+    AIR_CUDA(cudaMemcpyAsync(H->h_est + 3, H->scal + 3, sizeof(double), cudaMemcpyDeviceToHost, g.s));
+    return AIR_OK;
+}
+
+int air_gmres_after_cycle(AirGmres &g) {
+    air_hierarchy *H = g.H;
+    const double beta = sqrt(H->h_est[3]);
+    g.info->relres = beta / g.bnorm;
+    if (g.info->relres <= g.rtol) {
+        g.info->status = AIR_OK;
+        g.phase = AirGmres::DONE;
         return AIR_OK;
     }
-    int it = 0;
-    for (;;) {
-        // r = b - A x into V_0 and its norm
-        AIR_TRY(air_sell_spmv_f64(H->a0, x, H->V, b, s));
-        AIR_TRY(norm2(n, H->V, H->partials, nblk, sc + 3, s));
-        AIR_CUDA(cudaMemcpyAsync(H->h_est + 3, sc + 3, sizeof(double), cudaMemcpyDeviceToHost, s));
-        AIR_CUDA(cudaStreamSynchronize(s));
-        double beta = sqrt(H->h_est[3]);
-        info->relres = beta / bnorm;
-        if (info->relres <= rtol) { info->status = AIR_OK; break; }
-        if (it >= H->opt.max_iter) break;
-        AIR_TRY(air_scale_vec(n, H->V, H->V, sc + 3, 1, s));
-        AIR_CUDA(cudaMemsetAsync(H->gvec, 0, (size_t)(m + 1) * sizeof(double), s));
-        AIR_TRY(air_set_scalar(H->gvec, beta, s));
-        int k = 0;
-        for (int j = 0; j < m && it < H->opt.max_iter; ++j) {
-            double *vj = H->V + (int64_t)j * n, *zj = H->Z + (int64_t)j * n, *w = H->V + (int64_t)(j + 1) * n;
-            AIR_TRY(air_vcycle_run(H, vj, zj, s));
-            info->vcycles++;
-            AIR_TRY(air_sell_spmv_f64(H->a0, zj, w, nullptr, s));
-            // classical Gram-Schmidt, twice
-            AIR_TRY(air_dot_partials(n, H->V, n, j + 1, w, H->partials, nblk, s));
-            AIR_TRY(air_reduce_partials(j + 1, H->partials, nblk, h1, s));
-            AIR_TRY(air_update_dot_partials(n, H->V, n, j + 1, h1, w, H->partials, nblk, j + 1, s));
-            AIR_TRY(air_reduce_partials(j + 1, H->partials, nblk, h2, s));
-            AIR_TRY(air_update_dot_partials(n, H->V, n, j + 1, h2, w, H->partials, nblk, -1, s));
-            AIR_TRY(air_reduce_partials(1, H->partials, nblk, sc + 4, s));
-            AIR_TRY(air_arnoldi_givens(j, m, h1, h2, sc + 4, H->Hm, H->cs, H->sn, H->gvec, sc, bnorm, s));
-            AIR_TRY(air_scale_vec(n, w, w, sc + 2, 0, s));
-            AIR_CUDA(cudaMemcpyAsync(H->h_est + 1, sc + 1, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
-            AIR_CUDA(cudaStreamSynchronize(s));
-            ++it;
-            k = j + 1;
-            double est = H->h_est[1], hn = H->h_est[2];
-            if (est <= rtol || hn == 0.0 || !(est == est)) break;
-        }
-        AIR_TRY(air_hessenberg_solve(k, m, H->Hm, H->gvec, H->y, s));
-        AIR_TRY(air_axpy_multi(n, H->Z, n, k, H->y, x, s));
-        info->restarts++;
+    if (g.it >= H->opt.max_iter) {
+        g.phase = AirGmres::DONE;
+        return AIR_OK;
     }
-    info->iters = it;
+    AIR_TRY(air_scale_vec(g.n, H->V, H->V, H->scal + 3, 1, g.s));
+    AIR_CUDA(cudaMemsetAsync(H->gvec, 0, (size_t)(g.m + 1) * sizeof(double), g.s));
+    AIR_TRY(air_set_scalar(H->gvec, beta, g.s));
+    g.j = 0;
+    g.k = 0;
+    g.phase = AirGmres::STEP;
+    return AIR_OK;
+}
+
+// The vectors of Arnoldi step j: z_j = M^{-1} v_j is the V-cycle's part.
+double *air_gmres_vj(const AirGmres &g) { return g.H->V + (int64_t)g.j * g.n; }
+double *air_gmres_zj(const AirGmres &g) { return g.H->Z + (int64_t)g.j * g.n; }
+
+// Step j after its V-cycle: w = A z_j, CGS2 against V_0..V_j, Givens, v_{j+1}.
+int air_gmres_step(AirGmres &g) {
+    air_hierarchy *H = g.H;
+    const int64_t n = g.n;
+    const int j = g.j, m = g.m, nblk = g.nblk;
+    double *h1 = H->hcol, *h2 = H->hcol + (m + 2), *sc = H->scal;
+    double *zj = air_gmres_zj(g), *w = H->V + (int64_t)(j + 1) * n;
+    g.info->vcycles++;
+    AIR_TRY(air_sell_spmv_f64(H->a0, zj, w, nullptr, g.s));
+    AIR_TRY(air_dot_partials(n, H->V, n, j + 1, w, H->partials, nblk, g.s));
+    AIR_TRY(air_reduce_partials(j + 1, H->partials, nblk, h1, g.s));
+    AIR_TRY(air_update_dot_partials(n, H->V, n, j + 1, h1, w, H->partials, nblk, j + 1, g.s));
+    AIR_TRY(air_reduce_partials(j + 1, H->partials, nblk, h2, g.s));
+    AIR_TRY(air_update_dot_partials(n, H->V, n, j + 1, h2, w, H->partials, nblk, -1, g.s));
+    AIR_TRY(air_reduce_partials(1, H->partials, nblk, sc + 4, g.s));
+    AIR_TRY(air_arnoldi_givens(j, m, h1, h2, sc + 4, H->Hm, H->cs, H->sn, H->gvec, sc, g.bnorm, g.s));
+    AIR_TRY(air_scale_vec(n, w, w, sc + 2, 0, g.s));
+    AIR_CUDA(cudaMemcpyAsync(H->h_est + 1, sc + 1, 2 * sizeof(double), cudaMemcpyDeviceToHost, g.s));
+    return AIR_OK;
+}
+
+// After step j: end the cycle (solve the Hessenberg system, update x) when the
+// estimate meets the tolerance, on breakdown, after m steps or at max_iter.
+int air_gmres_after_step(AirGmres &g) {
+    air_hierarchy *H = g.H;
+    ++g.it;
+    g.k = g.j + 1;
+    const double est = H->h_est[1], hn = H->h_est[2];
+    if (est <= g.rtol || hn == 0.0 || !(est == est) || g.k >= g.m || g.it >= H->opt.max_iter) {
+        AIR_TRY(air_hessenberg_solve(g.k, g.m, H->Hm, H->gvec, H->y, g.s));
+        AIR_TRY(air_axpy_multi(g.n, H->Z, g.n, g.k, H->y, g.x, g.s));
+        g.info->restarts++;
+        g.phase = AirGmres::CYCLE;
+    } else {
+        ++g.j;
+    }
+    return AIR_OK;
+}
+
+int air_gmres_close(AirGmres &g) {
+    g.info->iters = g.it;
+    AIR_CUDA(cudaStreamSynchronize(g.s));
+    return g.info->status;
+}
+
+namespace {
+
+int gmres_impl(const AirLevel &A0, const air_hierarchy *Hc, const double *b, double *x, double rtol,
+               cudaStream_t s, air_solve_info *info) {
+    AirGmres g;
+    AIR_TRY(air_gmres_open(g, A0, Hc, b, x, rtol, s, info));
     AIR_CUDA(cudaStreamSynchronize(s));
-    return info->status;
+    air_gmres_after_open(g);
+    while (g.phase != AirGmres::DONE) {
+        if (g.phase == AirGmres::CYCLE) {
+            AIR_TRY(air_gmres_cycle(g));
+            AIR_CUDA(cudaStreamSynchronize(s));
+            AIR_TRY(air_gmres_after_cycle(g));
+        } else {
+            AIR_TRY(air_vcycle_run(g.H, air_gmres_vj(g), air_gmres_zj(g), s));
+            AIR_TRY(air_gmres_step(g));
+            AIR_CUDA(cudaStreamSynchronize(s));
+            AIR_TRY(air_gmres_after_step(g));
+        }
+    }
+    return air_gmres_close(g);
 }
 
 // Right-preconditioned BiCGSTAB (van der Vorst, 1992), the Krylov method the
@@ -599,6 +747,31 @@ int bicgstab_impl(const AirLevel &A0, const air_hierarchy *Hc, const double *b, 
 
 }  // namespace
 
+// The options of one setup (opt, or the defaults when null, with theta and
+// distance from the call), checked.
+int air_check_options(double theta, int distance, const air_options *opt, air_options *out) {
+    air_options &o = *out;
+    if (opt) o = *opt; else air_default_options(&o);
+    o.theta = theta;
+    o.distance = distance;
+    o.relax[sizeof(o.relax) - 1] = 0;
+    bool gs = false;
+    for (const char *c = o.relax; *c; ++c) {
+        if (!strchr("FCAfca", *c)) return AIR_ERR_INVALID_ARG;
+        gs = gs || (*c >= 'a');
+    }
+    if (gs && o.precision == AIR_PREC_BF16) return AIR_ERR_UNSUPPORTED;
+    if (!(theta >= 0.0) || !(theta <= 1.0) || !(o.theta_r <= 1.0) || o.max_levels < 1 || o.max_levels > AIR_MAX_LEVELS ||
+        o.max_dense < 1 || o.restart < 1 || o.restart > 32 || o.max_iter < 0 || o.falgout_block < 0 ||
+        (o.falgout_block > 0 && (o.falgout_block % 1024 != 0 || o.falgout_block > 8192)) || o.block_size < 0 ||
+        o.block_size > 16 ||
+        (o.precision != AIR_PREC_F64 && o.precision != AIR_PREC_F32 && o.precision != AIR_PREC_BF16))
+        return AIR_ERR_INVALID_ARG;
+    if (distance < 1) return AIR_ERR_INVALID_ARG;
+    if (distance > 2) return AIR_ERR_UNSUPPORTED;
+    return AIR_OK;
+}
+
 extern "C" {
 
 void air_default_options(air_options *o) {
@@ -629,24 +802,8 @@ int air_setup(const air_csr *A, double theta, int distance, const air_options *o
         A->n_rows > INT32_MAX)
         return AIR_ERR_INVALID_ARG;
     air_options o;
-    if (opt) o = *opt; else air_default_options(&o);
-    o.theta = theta;
-    o.distance = distance;
-    o.relax[sizeof(o.relax) - 1] = 0;
-    bool gs = false;
-    for (const char *c = o.relax; *c; ++c) {
-        if (!strchr("FCAfca", *c)) return AIR_ERR_INVALID_ARG;
-        gs = gs || (*c >= 'a');
-    }
-    if (gs && o.precision == AIR_PREC_BF16) return AIR_ERR_UNSUPPORTED;
-    if (!(theta >= 0.0) || !(theta <= 1.0) || !(o.theta_r <= 1.0) || o.max_levels < 1 || o.max_levels > AIR_MAX_LEVELS ||
-        o.max_dense < 1 || o.restart < 1 || o.restart > 32 || o.max_iter < 0 || o.falgout_block < 0 ||
-        (o.falgout_block > 0 && (o.falgout_block % 1024 != 0 || o.falgout_block > 8192)) || o.block_size < 0 ||
-        o.block_size > 16 ||
-        (o.precision != AIR_PREC_F64 && o.precision != AIR_PREC_F32 && o.precision != AIR_PREC_BF16))
-        return AIR_ERR_INVALID_ARG;
-    if (distance < 1) return AIR_ERR_INVALID_ARG;
-    if (distance > 2) return AIR_ERR_UNSUPPORTED;
+    const int oc = air_check_options(theta, distance, opt, &o);
+    if (oc != AIR_OK) return oc;
     air_hierarchy *H = new (std::nothrow) air_hierarchy();
     if (!H) return AIR_ERR_OOM;
     AirCallStream call((cudaStream_t)stream);

@@ -192,6 +192,64 @@ struct air_hierarchy {
     float *mc32 = nullptr;
 };
 
+// Scratch carried between the halves of one coarsening step (air_api.cu):
+// the splitting half leaves the local l-AIR solves of LS ready to run.
+struct AirCoarsen {
+    int stop = 0;                    // level l is the coarsest; nothing is kept
+    int32_t *cnt = nullptr, *dmax = nullptr, *rsci = nullptr;
+    int64_t *scanw = nullptr, *rsrp = nullptr, *dsing = nullptr;
+    AirLevel LS;                     // level l with R's strength graph
+};
+int air_check_options(double theta, int distance, const air_options *opt, air_options *out);
+int air_setup_begin(const air_csr *A, const air_options *opt, cudaStream_t s, air_hierarchy *H);
+bool air_setup_is_coarsest(const air_hierarchy *H, int l);
+int air_coarsen_split(air_hierarchy *H, int l, cudaStream_t s, AirCoarsen *c);
+int air_coarsen_lair(air_hierarchy *H, int l, cudaStream_t s, AirCoarsen *c);
+int air_coarsen_finish(air_hierarchy *H, int l, cudaStream_t s, AirCoarsen *c);
+int air_setup_end(air_hierarchy *H, cudaStream_t s);
+void air_add_phase_ms(air_hierarchy *H, int phase, double ms);
+// The local l-AIR solves of several levels (of independent hierarchies) in one
+// launch; levels[k] with R's strength graph, max_m[k] its largest
+// neighbourhood, d_nsing[k] its count of singular systems.
+int air_lair_solve_batch(int count, const AirLevel *const *levels, const int32_t *max_m, int distance,
+                         int64_t *const *d_nsing, cudaStream_t s);
+
+// One flexible GMRES solve split at its host reads (air_api.cu).
+struct AirGmres {
+    enum Phase { OPENED, CYCLE, STEP, DONE };
+    air_hierarchy *H = nullptr;
+    const AirLevel *A0 = nullptr;
+    const double *b = nullptr;
+    double *x = nullptr;
+    double rtol = 0.0, bnorm = 0.0;
+    cudaStream_t s = nullptr;
+    air_solve_info *info = nullptr;
+    int64_t n = 0;
+    int m = 0, nblk = 0, it = 0, j = 0, k = 0;
+    Phase phase = OPENED;
+};
+int air_gmres_open(AirGmres &g, const AirLevel &A0, const air_hierarchy *H, const double *b, double *x,
+                   double rtol, cudaStream_t s, air_solve_info *info);
+void air_gmres_after_open(AirGmres &g);
+int air_gmres_cycle(AirGmres &g);
+int air_gmres_after_cycle(AirGmres &g);
+double *air_gmres_vj(const AirGmres &g);
+double *air_gmres_zj(const AirGmres &g);
+int air_gmres_step(AirGmres &g);
+int air_gmres_after_step(AirGmres &g);
+int air_gmres_close(AirGmres &g);
+// The V-cycle from lev[0].b to lev[0].x (the hierarchy's own precision, no graph).
+int air_vcycle_staged(air_hierarchy *H, cudaStream_t s);
+// Conversions between caller vectors (FP64) and hierarchies' lev[0] buffers, several at once.
+struct AirConvJob {
+    const void *src;
+    void *dst;
+    int64_t n;       // 0: skip
+    int mode;        // 0 FP64 copy, 1 FP64 -> FP32, 2 FP32 -> FP64
+};
+int air_convert_batch(int count, const AirConvJob *d_jobs, cudaStream_t s);
+
+
 // ------------------------------------------------------------------ launchers
 // scan.cu
 int air_exclusive_scan_i32(const int32_t *in, int64_t *out, int64_t n, cudaStream_t s);

@@ -307,14 +307,23 @@ __global__ void __launch_bounds__(32) rs5_warp_kernel(RS5Args a) {
     uint32_t pe0 = 0u, pe1 = 0u;
     uint64_t pm0 = 0ull, pm1 = 0ull;
     while (true) {
-        // ---- the pick: lowest member of the highest non-empty bucket
-        while (top >= 1 && s.pop[top] == 0) --top;
-        if (top < 1) break;
-        const int B = top;
-        if (s.pl[B] < s.cl[B]) {
+        // ---- the pick: lowest member of the highest non-empty bucket (the state
+        // of the previous top bucket is read at once: it usually still has members)
+        int B = top;
+        int32_t popB = s.pop[B], plB = s.pl[B], clB = s.cl[B];
+        uint32_t wv = lane < 16 ? s.cv[B * 16 + lane] : 0u;
+        if (popB == 0) {
+            while (top >= 1 && s.pop[top] == 0) --top;
+            if (top < 1) break;
+            B = top;
+            plB = s.pl[B];
+            clB = s.cl[B];
+            wv = lane < 16 ? s.cv[B * 16 + lane] : 0u;
+        }
+        if (plB < clB) {
             // insertions below the cursor: move it down to the lowest of them and
             // read that line (the bucket has no members below it)
-            const int32_t line = s.pl[B];
+            const int32_t line = plB;
             const uint64_t lw = lane < 8 ? __ldcg((const unsigned long long *)&a.L0[(int64_t)B * a.w0 + line * 8 + lane]) : 0ull;
             if (lane < 8) {
                 s.cv[B * 16 + 2 * lane] = (uint32_t)lw;
@@ -324,19 +333,21 @@ __global__ void __launch_bounds__(32) rs5_warp_kernel(RS5Args a) {
             if (lane == 0) { s.cl[B] = line; s.pl[B] = CL_INF; }
             ++moves;
             __syncwarp();
+            clB = line;
+            wv = lane < 16 ? s.cv[B * 16 + lane] : 0u;
         }
-        uint32_t wv = lane < 16 ? s.cv[B * 16 + lane] : 0u;
         unsigned bal = __ballot_sync(FULL, wv != 0u);
         if (bal == 0u) {
             ++refills;
             if (!rs5_refill(a, s, B, &steps, &visits)) { failed = true; break; }
             wv = lane < 16 ? s.cv[B * 16 + lane] : 0u;
+            clB = s.cl[B];
             bal = __ballot_sync(FULL, wv != 0u);
             if (bal == 0u) { failed = true; break; }
         }
         const int sw = __ffs(bal) - 1;
         const uint32_t word = __shfl_sync(FULL, wv, sw);
-        const int32_t lbase = s.cl[B] * 512;
+        const int32_t lbase = clB * 512;
         const int32_t i = lbase + sw * 32 + (__ffs(word) - 1);
         if (++picks > (unsigned long long)a.n || i >= a.n) { failed = true; break; }
         // the next member of the same line is the likely next pick

@@ -8,6 +8,8 @@
 #include <float.h>
 #include <math.h>
 
+#include <vector>
+
 #include "air_internal.cuh"
 
 namespace cg = cooperative_groups;
@@ -745,19 +747,37 @@ __device__ __forceinline__ int find_sorted(const int32_t *arr, int m, int32_t ke
 // LU with partial pivoting (ties -> smallest row), forward substitution in
 // ascending and back substitution in descending column order, all with
 // explicitly rounded operations.  |pivot| <= 1e-14 max|M| -> z = 0.
-__global__ void lair_solve_kernel(int64_t nc, const int32_t *crows, const int64_t *rp, const int32_t *ci,
-                                  const double *v, const int64_t *srp, const int32_t *sci, const int8_t *cf,
-                                  const int64_t *rrp, int32_t *rci, double *rv, int maxm, int ld, int distance,
-                                  unsigned long long *nsing) {
-    extern __shared__ double lsm[];
-    int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int nints = distance >= 2 ? LAIR_CAP : maxm;
-    int64_t per_warp = (int64_t)maxm * ld + maxm + (nints + 1) / 2 + 1;   // doubles
-    double *M = lsm + wib * per_warp;
-    double *z = M + (int64_t)maxm * ld;
-    int32_t *N = (int32_t *)(z + maxm);
-    for (int64_t t = global_warp(); t < nc; t += warp_count()) {
-        int32_t i = crows[t];
+// One level's arrays for the local solves (one job of a batched launch).
+struct LairJob {
+    int64_t first;                   // index of the job's first system in the launch
+    int64_t nc;
+    const int32_t *crows;
+    const int64_t *rp;
+    const int32_t *ci;
+    const double *v;
+    const int64_t *srp;
+    const int32_t *sci;
+    const int8_t *cf;
+    const int64_t *rrp;
+    int32_t *rci;
+    double *rv;
+    unsigned long long *nsing;
+};
+
+// The local system of C point crows[t] of job J, solved by one warp in the
+// warp's shared-memory slot (M: maxm x ld, z: maxm, N: the neighbourhood).
+__device__ void lair_solve_one(const LairJob &J, int64_t t, int maxm, int ld, int distance, double *M, double *z,
+                               int32_t *N) {
+    const int lane = threadIdx.x & 31;
+    const int64_t *rp = J.rp, *srp = J.srp, *rrp = J.rrp;
+    const int32_t *ci = J.ci, *sci = J.sci;
+    const double *v = J.v;
+    const int8_t *cf = J.cf;
+    int32_t *rci = J.rci;
+    double *rv = J.rv;
+    unsigned long long *nsing = J.nsing;
+    {
+        int32_t i = J.crows[t];
         // neighbourhood
         int m = 0;
         if (distance >= 2) {
@@ -862,6 +882,38 @@ __global__ void lair_solve_kernel(int64_t nc, const int32_t *crows, const int64_
         }
         if (lane == 0) { rci[pos + before] = i; rv[pos + before] = 1.0; }
         __syncwarp();
+    }
+}
+
+// Shared-memory slot of this warp: M, z, N (doubles per warp as in air_lair_solve).
+__device__ __forceinline__ double *lair_slot(int maxm, int ld, int distance) {
+    extern __shared__ double lsm[];
+    const int nints = distance >= 2 ? LAIR_CAP : maxm;
+    const int64_t per_warp = (int64_t)maxm * ld + maxm + (nints + 1) / 2 + 1;
+    return lsm + (threadIdx.x >> 5) * per_warp;
+}
+
+__global__ void lair_solve_kernel(LairJob J, int maxm, int ld, int distance) {
+    double *M = lair_slot(maxm, ld, distance);
+    double *z = M + (int64_t)maxm * ld;
+    int32_t *N = (int32_t *)(z + maxm);
+    for (int64_t t = global_warp(); t < J.nc; t += warp_count()) lair_solve_one(J, t, maxm, ld, distance, M, z, N);
+}
+
+// The systems of several jobs as one index range: system t belongs to the last
+// job whose first index is <= t.
+__global__ void lair_solve_batch_kernel(int njobs, const LairJob *jobs, int64_t total, int maxm, int ld,
+                                        int distance) {
+    double *M = lair_slot(maxm, ld, distance);
+    double *z = M + (int64_t)maxm * ld;
+    int32_t *N = (int32_t *)(z + maxm);
+    for (int64_t t = global_warp(); t < total; t += warp_count()) {
+        int lo = 0, hi = njobs - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) / 2;
+            if (jobs[mid].first <= t) lo = mid; else hi = mid - 1;
+        }
+        lair_solve_one(jobs[lo], t - jobs[lo].first, maxm, ld, distance, M, z, N);
     }
 }
 
@@ -1296,26 +1348,73 @@ int air_lair_counts(int64_t nc, const int32_t *crows, const int64_t *srp, const 
     return AIR_OK;
 }
 
-int air_lair_solve(const AirLevel &L, int32_t max_m, int distance, int64_t *d_nsing, cudaStream_t s) {
-    int maxm = max_m < 1 ? 1 : max_m;
-    int ld = maxm | 1;
-    const int nints = distance >= 2 ? LAIR_CAP : maxm;
-    size_t per_warp = ((size_t)maxm * ld + maxm + (nints + 1) / 2 + 1) * sizeof(double);
-    int warps = (int)(((distance >= 2 ? AIR_SMEM_OPTIN : 96 * 1024)) / per_warp);
-    if (warps > 8) warps = 8;
-    if (warps < 1) {
+namespace {
+
+LairJob lair_job(const AirLevel &L, int64_t *d_nsing, int64_t first) {
+    return LairJob{first, L.nc, L.crows, L.rp, L.ci, L.v, L.srp, L.sci, L.cf, L.rrp, L.rci, L.rv,
+                   (unsigned long long *)d_nsing};
+}
+
+// Warps per block and shared memory of a local-solve launch for neighbourhoods up to max_m.
+int lair_shape(int32_t max_m, int distance, int *maxm, int *ld, int *warps, size_t *smem) {
+    *maxm = max_m < 1 ? 1 : max_m;
+    *ld = *maxm | 1;
+    const int nints = distance >= 2 ? LAIR_CAP : *maxm;
+    const size_t per_warp = ((size_t)*maxm * *ld + *maxm + (nints + 1) / 2 + 1) * sizeof(double);
+    *warps = (int)(((distance >= 2 ? AIR_SMEM_OPTIN : 96 * 1024)) / per_warp);
+    if (*warps > 8) *warps = 8;
+    if (*warps < 1) {
         if (per_warp > AIR_SMEM_OPTIN) return AIR_ERR_UNSUPPORTED;
-        warps = 1;
+        *warps = 1;
     }
-    size_t smem = per_warp * warps;
-    AIR_CUDA(cudaFuncSetAttribute(lair_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, AIR_SMEM_OPTIN));
-    int64_t blocks = (L.nc + warps - 1) / warps;
+    *smem = per_warp * *warps;
+    return AIR_OK;
+}
+
+unsigned lair_blocks(int64_t systems, int warps) {
+    int64_t blocks = (systems + warps - 1) / warps;
     if (blocks > 152 * 16) blocks = 152 * 16;
     if (blocks < 1) blocks = 1;
-    lair_solve_kernel<<<air_counted((unsigned)blocks), warps * 32, smem, s>>>(L.nc, L.crows, L.rp, L.ci, L.v, L.srp, L.sci, L.cf,
-                                                                L.rrp, L.rci, L.rv, maxm, ld, distance,
-                                                                (unsigned long long *)d_nsing);
+    return (unsigned)blocks;
+}
+
+}  // namespace
+
+int air_lair_solve(const AirLevel &L, int32_t max_m, int distance, int64_t *d_nsing, cudaStream_t s) {
+    int maxm = 0, ld = 0, warps = 0;
+    size_t smem = 0;
+    AIR_TRY(lair_shape(max_m, distance, &maxm, &ld, &warps, &smem));
+    AIR_CUDA(cudaFuncSetAttribute(lair_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, AIR_SMEM_OPTIN));
+    lair_solve_kernel<<<air_counted(lair_blocks(L.nc, warps)), warps * 32, smem, s>>>(lair_job(L, d_nsing, 0), maxm,
+                                                                                         ld, distance);
     AIR_LAUNCH();
+    return AIR_OK;
+}
+
+int air_lair_solve_batch(int count, const AirLevel *const *levels, const int32_t *max_m, int distance,
+                         int64_t *const *d_nsing, cudaStream_t s) {
+    if (count <= 0) return AIR_OK;
+    std::vector<LairJob> jobs((size_t)count);
+    int32_t mm = 0;
+    int64_t total = 0;
+    for (int k = 0; k < count; ++k) {
+        jobs[(size_t)k] = lair_job(*levels[k], d_nsing[k], total);
+        total += levels[k]->nc;
+        mm = max_m[k] > mm ? max_m[k] : mm;
+    }
+    int maxm = 0, ld = 0, warps = 0;
+    size_t smem = 0;
+    AIR_TRY(lair_shape(mm, distance, &maxm, &ld, &warps, &smem));
+    LairJob *d_jobs = nullptr;
+    AIR_CUDA(cudaMallocAsync(&d_jobs, (size_t)count * sizeof(LairJob), s));
+    AIR_CUDA(cudaMemcpyAsync(d_jobs, jobs.data(), (size_t)count * sizeof(LairJob), cudaMemcpyHostToDevice, s));
+    AIR_CUDA(cudaFuncSetAttribute(lair_solve_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  AIR_SMEM_OPTIN));
+    lair_solve_batch_kernel<<<air_counted(lair_blocks(total, warps)), warps * 32, smem, s>>>(count, d_jobs, total,
+                                                                                                maxm, ld, distance);
+    AIR_LAUNCH();
+    AIR_CUDA(cudaStreamSynchronize(s));     // the job table is read from pageable host memory
+    cudaFreeAsync(d_jobs, s);
     return AIR_OK;
 }
 

@@ -827,6 +827,38 @@ int vcycle_graph(air_hierarchy *H, cudaStream_t s) {
     return vcycle_t<TV, T>(H, (const T *)L0.b, (T *)L0.x, s);
 }
 
+int air_vcycle_staged(air_hierarchy *H, cudaStream_t s) {
+    const AirLevel &L0 = H->lev[0];
+    if (H->opt.precision == AIR_PREC_F64) return vcycle_t<double, double>(H, (const double *)L0.b, (double *)L0.x, s);
+    if (H->opt.precision == AIR_PREC_BF16)
+        return vcycle_t<__nv_bfloat16, float>(H, (const float *)L0.b, (float *)L0.x, s);
+    return vcycle_t<float, float>(H, (const float *)L0.b, (float *)L0.x, s);
+}
+
+namespace {
+
+// Job blockIdx.y: the same element conversions as d2f_kernel / f2d_kernel, or a copy.
+__global__ void convert_batch_kernel(const AirConvJob *jobs) {
+    const AirConvJob J = jobs[blockIdx.y];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < J.n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (J.mode == 1) ((float *)J.dst)[i] = (float)((const double *)J.src)[i];
+        else if (J.mode == 2) ((double *)J.dst)[i] = (double)((const float *)J.src)[i];
+        else ((double *)J.dst)[i] = ((const double *)J.src)[i];
+    }
+}
+
+}  // namespace
+
+int air_convert_batch(int count, const AirConvJob *d_jobs, cudaStream_t s) {
+    if (count <= 0) return AIR_OK;
+    if (count > 65535) return AIR_ERR_INVALID_ARG;
+    unsigned bx = (unsigned)((152 * 8 + count - 1) / count);
+    dim3 grid(bx < 1 ? 1 : bx, (unsigned)count);
+    convert_batch_kernel<<<air_counted(grid), 256, 0, s>>>(d_jobs);
+    AIR_LAUNCH();
+    return AIR_OK;
+}
+
 int air_vcycle_run(const air_hierarchy *Hc, const double *b, double *x, cudaStream_t s, int use_graph) {
     air_hierarchy *H = const_cast<air_hierarchy *>(Hc);
     const AirLevel &L0 = H->lev[0];

@@ -109,3 +109,36 @@ def test_concurrent_setups_overlap():
     t_bat = time.perf_counter() - t0
     assert st == [0] * 4
     assert t_bat < 0.7 * t_seq, (t_bat, t_seq)
+
+
+def test_setup_batch_distance2_equals_single_setups():
+    ss = _systems()[:3]
+    As = [air.CSR.from_host(s.row_ptr, s.col, s.val) for s in ss]
+    Hs, st = air.setup_batch(As, theta=0.25, distance=2, max_coarse=100)
+    assert st == [0] * len(ss)
+    for A, H in zip(As, Hs):
+        _levels_equal(H, air.setup(A, theta=0.25, distance=2, max_coarse=100))
+
+
+def test_solve_batch_mixed_hierarchies_restarts_and_stops():
+    # FP64, FP32 and BF16 hierarchies in one batch; GMRES(4) so that cycles end
+    # and restart at different rounds; one problem stopped by max_iter and one
+    # with a zero right-hand side; each must equal its single-problem solve
+    ss = _systems()[:4]
+    As = [air.CSR.from_host(s.row_ptr, s.col, s.val) for s in ss]
+    opts = [dict(precision=0, restart=4), dict(precision=1, restart=4),
+            dict(precision=2, restart=30, max_iter=3), dict(precision=1, restart=4)]
+    Hs = [air.setup(A, theta=0.25, max_coarse=100, **o) for A, o in zip(As, opts)]
+    bs = [torch.from_numpy(np.ascontiguousarray(s.rhs)).cuda() for s in ss]
+    bs[3] = torch.zeros_like(bs[3])
+    xs, infos, st = air.gmres_solve_batch(As, Hs, bs, rtol=1e-8)
+    assert st[0] == 0 and st[1] == 0 and st[3] == 0 and st[2] == 1, st
+    assert infos[2].iters == 3 and infos[3].iters == 0
+    assert infos[0].restarts > 1 and infos[1].restarts > 1
+    for A, H, b, x, inf in zip(As, Hs, bs, xs, infos):
+        x1, inf1 = air.gmres_solve(A, H, b, rtol=1e-8)
+        torch.cuda.synchronize()
+        assert (inf.iters, inf.restarts, inf.vcycles) == (inf1.iters, inf1.restarts, inf1.vcycles)
+        assert inf.relres == inf1.relres
+        assert torch.equal(x, x1)
+    assert float(xs[3].abs().max()) == 0.0
