@@ -155,29 +155,32 @@ class ClockSampler:
 
 # ------------------------------------------------------- algorithmic bytes
 def vcycle_bytes(H, wbytes, diag_bytes=0):
-    """Algorithmic DRAM bytes of one V-cycle: each array read once per use.
+    """Algorithmic DRAM bytes of one V-cycle (relaxation FCF): each array read
+    once per use.
 
     Per non-coarsest level (n rows, nnz z = z_F + z_C, R with nnz_R entries,
-    n_C coarse points, w = value bytes):
-      restriction   nnz_R (w+4) + 8 n_C + w n + w n_C
-      F sweep (+P)  z_F (w+4) + 8 n_F + 4 n + w n_C + 2 w n_F + n + w n
-      C sweep       z_C (w+4) + 8 n_C + w n + 2 w n_C + n + w n
-      F sweep       z_F (w+4) + 8 n_F + w n + 2 w n_F + n + w n
-    A level stored in the block form (facet blocks of b) reads per row set
-    (z - rows) w + 4 (z - rows) / b + x rows for the matrix instead of z (w+4)
-    (the standalone diagonal one per row, in the vector type x).
-    coarsest: w n_L^2 + 2 w n_L.  BF16 storage (w = 2) adds the FP32
-    diagonal (4 B per relaxed row) and keeps FP32 vectors (counted as w = 4
-    for vectors).
+    n_C coarse points, w = value bytes, x = vector element bytes):
+      restriction     nnz_R (w+4) + 8 n_C + x n + x n_C
+      interpolation   4 n (P's columns) + x n_C + x n
+      sweep over a point set S of m_S rows (F, C, F), from one full vector
+      into the other: the set's matrix, 4 B of row index for every row (the
+      set's rows and the copied rows of the other set), b and 1/a_ii of the
+      set, the old vector read and the new one written in full:
+                      mat(z_S, m_S) + 4 n + 2 x m_S + 2 x n
+    mat(z, m) = z (w+4) in the entry form; a level stored in the block form
+    (facet blocks of b) reads (z - m) w + 4 (z - m) / b + x m instead (the
+    standalone diagonal one per row, in the vector type).  coarsest: x n_L^2 +
+    2 x n_L.  BF16 storage (w = 2) keeps FP32 vectors (x = 4) and adds the FP32
+    diagonal (diag_bytes per relaxed row).
     """
     total = 0
     L = H.levels()
     for l in range(L):
         inf = H.info(l)
         n = inf.n
+        x = 4 if wbytes == 2 else wbytes  # vector element bytes
         if inf.coarsest:
-            xb = 4 if wbytes == 2 else wbytes
-            total += xb * n * n + 2 * xb * n
+            total += x * n * n + 2 * x * n
             continue
         rp = H.export(l, "A.row_ptr")
         cf = H.export(l, "cf").astype(bool)
@@ -187,19 +190,18 @@ def vcycle_bytes(H, wbytes, diag_bytes=0):
         nc = int(cf.sum())
         nf = n - nc
         w = wbytes                       # stored value bytes
-        x = 4 if wbytes == 2 else wbytes  # vector element bytes
         bsz = inf.block_size
 
         def mat(z, rows):
-            # entry form: value + 4 B column per entry; block form: the b values of every
-            # block with one 4 B column per block, the standalone diagonal in the vector type
             if not bsz:
                 return z * (w + 4)
             return (z - rows) * w + (z - rows) // bsz * 4 + rows * x
+
+        def sweep(z, m):
+            return mat(z, m) + 4 * n + 2 * x * m + 2 * x * n + diag_bytes * m
         total += inf.nnz_r * (w + 4) + 8 * nc + x * n + x * nc
-        total += mat(zf, nf) + 8 * nf + 4 * n + x * nc + 2 * x * nf + n + x * n + diag_bytes * nf
-        total += mat(zc, nc) + 8 * nc + x * n + 2 * x * nc + n + x * n + diag_bytes * nc
-        total += mat(zf, nf) + 8 * nf + x * n + 2 * x * nf + n + x * n + diag_bytes * nf
+        total += 4 * n + x * nc + x * n
+        total += sweep(zf, nf) + sweep(zc, nc) + sweep(zf, nf)
     return total
 
 
@@ -237,6 +239,16 @@ def median_time(fn, stream, reps, runs=5):
 
 def spmv_bytes(n, nnz):
     return nnz * 12 + (n + 1) * 8 + n * 8 + n * 8
+
+
+def krylov_spmv_bytes(n, nnz, b):
+    """Algorithmic bytes of y = A x with the FP64 copy of A the Krylov solves use:
+    block form (facet blocks of b): the off-diagonal blocks' values, one 4 B
+    column per block, the standalone diagonal, x read once, y written; entry
+    form (b = 0): 12 B per entry plus x and y."""
+    if not b:
+        return nnz * 12 + 16 * n
+    return (nnz - n) * 8 + (nnz - n) // b * 4 + 8 * n + 16 * n
 
 
 # ------------------------------------------------------------ GPU assembly
@@ -477,6 +489,7 @@ def run_ours(args):
     # V-cycle and SpMV roofline (FP32 hierarchy is the reported form)
     gbs_peak, peak_kind = peaks()
     rl = {}
+    kry = {"s": None, "block_size": 0}
     breakdown = {}
     for prec, key in ((1, "f32"), (0, "f64"), (2, "bf16")):
         torch.cuda.synchronize()
@@ -508,6 +521,13 @@ def run_ours(args):
         for _ in range(3):
             H.vcycle(b, xv)
         t = median_time(lambda: H.vcycle(b, xv), stream, args.vcycles)
+        if key == "f32":
+            # the Krylov solves' matrix product: the hierarchy's FP64 copy of A
+            yk = torch.empty_like(b)
+            for _ in range(3):
+                H.spmv(b, yk)
+            kry["s"] = median_time(lambda: H.spmv(b, yk), stream, args.vcycles)
+            kry["block_size"] = H.info(0).block_size
         rl[key] = {"bytes": vb, "s": t, "gbs": vb / t / 1e9, "levels": H.levels(),
                    "lanes_per_row": [[H.info(l).lanes_f, H.info(l).lanes_c, H.info(l).lanes_r]
                                      for l in range(H.levels() - 1)],
@@ -518,6 +538,7 @@ def run_ours(args):
         air.spmv(A, b, y)
     t_spmv = median_time(lambda: air.spmv(A, b, y), stream, args.vcycles)
     sb = spmv_bytes(s.n, s.nnz)
+    kb = krylov_spmv_bytes(s.n, s.nnz, kry["block_size"])
 
     # the paper's coarsening as a variant: Falgout-style splitting (blocks of consecutive points)
     falgout = None
@@ -645,9 +666,15 @@ def run_ours(args):
                      "achieved": v32["gbs"], "peak": gbs_peak, "unit": "GB/s",
                      "frac": v32["gbs"] / gbs_peak, "traffic": vcycle_traffic(v32["bytes"]),
                      "algorithmic_bytes": v32["bytes"], "launch_s": v32["s"], "peak_kind": peak_kind},
-        "roofline_spmv": {"bound": "hbm", "kernel": "row_kernel<4,U,double,double,0> (air_spmv: CSR, 4 lanes per row)",
-                          "achieved": sb / t_spmv / 1e9, "peak": gbs_peak, "unit": "GB/s",
-                          "frac": sb / t_spmv / 1e9 / gbs_peak, "algorithmic_bytes": sb, "launch_s": t_spmv},
+        "roofline_spmv": {"bound": "hbm",
+                          "kernel": (f"bsell_kernel<{kry['block_size']},...,double,double,0> (air_hierarchy_spmv: "
+                                     "the FGMRES matrix product, FP64 block layout)") if kry["block_size"] else
+                                    "sell_kernel<8,double,double,0> (air_hierarchy_spmv: the FGMRES matrix product)",
+                          "achieved": kb / kry["s"] / 1e9, "peak": gbs_peak, "unit": "GB/s",
+                          "frac": kb / kry["s"] / 1e9 / gbs_peak, "algorithmic_bytes": kb, "launch_s": kry["s"],
+                          "csr_air_spmv": {"kernel": "row_kernel<4,U,double,double,0> (air_spmv: CSR, 4 lanes per row)",
+                                           "achieved": sb / t_spmv / 1e9, "frac": sb / t_spmv / 1e9 / gbs_peak,
+                                           "algorithmic_bytes": sb, "launch_s": t_spmv}},
         "breakdown": breakdown,
         "bicgstab_f64_hierarchy": bic,
         "dominant_kernel": {

@@ -154,6 +154,13 @@ int air_vcycle(const air_hierarchy *H, const double *b, double *x, void *stream)
 /* y = A x for device CSR A and device vectors.  Asynchronous. */
 int air_spmv(const air_csr *A, const double *x, double *y, void *stream);
 
+/* y = A x with the FP64 copy of the finest operator that the hierarchy keeps
+ * for the Krylov solves (the block layout when opt->block_size was set, else
+ * SELL-32): the matrix product inside air_gmres_solve (Section 5.1).  x and y
+ * are device float64 vectors of length n, distinct.  Asynchronous on stream.
+ * INVALID_ARG for a NULL argument. */
+int air_hierarchy_spmv(const air_hierarchy *H, const double *x, double *y, void *stream);
+
 /* BiCGSTAB preconditioned on the right by one V-cycle of H (van der Vorst,
  * 1992): the Krylov method of the paper's experiments (Section 5.1, Table 2,
  * stopping at relative residual 1e-12).  x0 = 0, shadow residual r0 = b.  It

@@ -27,7 +27,8 @@ EXPORTED = ["air_default_options", "air_setup", "air_vcycle", "air_spmv", "air_g
             "air_csr_transpose", "air_csr_outer", "air_setup_batch", "air_gmres_solve_batch",
             "air_bicgstab_solve", "air_vcycle_multi", "air_bicgstab_solve_multi",
             "air_vcycle_multi_f32", "air_hdg_points", "air_hdg_size", "air_hdg_assemble",
-            "air_hdg_velocity_gradient", "air_csr_transpose_scaled", "air_block_diag_apply"]
+            "air_hdg_velocity_gradient", "air_csr_transpose_scaled", "air_block_diag_apply",
+            "air_hierarchy_spmv"]
 
 
 class air_csr(C.Structure):
@@ -101,6 +102,8 @@ def lib() -> C.CDLL:
     L.air_vcycle.restype = C.c_int
     L.air_spmv.argtypes = [C.POINTER(air_csr), C.c_void_p, C.c_void_p, C.c_void_p]
     L.air_spmv.restype = C.c_int
+    L.air_hierarchy_spmv.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    L.air_hierarchy_spmv.restype = C.c_int
     L.air_gmres_solve.argtypes = [C.POINTER(air_csr), C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
                                   C.c_void_p, C.POINTER(air_solve_info)]
     L.air_gmres_solve.restype = C.c_int
@@ -268,6 +271,15 @@ class Hierarchy:
             _check(lib().air_hierarchy_export(self._h, level, code, out.ctypes.data_as(C.c_void_p)),
                    f"air_hierarchy_export({what})")
         return out
+
+    def spmv(self, x, y=None, stream=None):
+        """air_hierarchy_spmv: y = A x with the FP64 copy of A the Krylov solves use."""
+        import torch
+        if y is None:
+            y = torch.empty_like(x)
+        _check(lib().air_hierarchy_spmv(self._h, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
+                                        C.c_void_p(_stream(stream))), "air_hierarchy_spmv")
+        return y
 
     def vcycle(self, b, x=None, stream=None):
         import torch

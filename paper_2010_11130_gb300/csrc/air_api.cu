@@ -7,7 +7,10 @@
 #include <string.h>
 
 #include <atomic>
+#include <mutex>
 #include <new>
+#include <set>
+#include <utility>
 
 #include "air_internal.cuh"
 
@@ -19,6 +22,19 @@ void air_launch_counter_sub(unsigned long long k) { g_launches.fetch_sub(k); }
 AirCallSlot &air_call_slot() {
     thread_local AirCallSlot slot;
     return slot;
+}
+
+cudaError_t air_smem_optin_impl(const void *f) {
+    static std::mutex mu;
+    static std::set<std::pair<int, const void *>> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done.count({dev, f})) return cudaSuccess;
+    e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, AIR_SMEM_OPTIN);
+    if (e == cudaSuccess) done.insert({dev, f});
+    return e;
 }
 
 cudaError_t air_dmalloc(void **p, size_t bytes) {
@@ -48,7 +64,10 @@ void dfree(T *&p) {
     p = nullptr;
 }
 
+// Small reads into pageable host memory wait for the stream first, so that the
+// copy itself never waits on a long kernel (other host threads keep launching).
 int read_i64(const int64_t *d, int64_t *h, cudaStream_t s) {
+    AIR_CUDA(cudaStreamSynchronize(s));
     AIR_CUDA(cudaMemcpyAsync(h, d, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     AIR_CUDA(cudaStreamSynchronize(s));
     return AIR_OK;
@@ -56,6 +75,7 @@ int read_i64(const int64_t *d, int64_t *h, cudaStream_t s) {
 
 int check_err(air_hierarchy *H, cudaStream_t s) {
     int e = 0;
+    AIR_CUDA(cudaStreamSynchronize(s));
     AIR_CUDA(cudaMemcpyAsync(&e, H->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     AIR_CUDA(cudaStreamSynchronize(s));
     if (e & AIR_DEVERR_CSR) return AIR_ERR_CSR_MALFORMED;
@@ -826,6 +846,11 @@ int air_vcycle(const air_hierarchy *H, const double *b, double *x, void *stream)
 int air_spmv(const air_csr *A, const double *x, double *y, void *stream) {
     if (!A || !x || !y || !A->on_device || A->n_rows <= 0) return AIR_ERR_INVALID_ARG;
     return air_spmv_f64(A->n_rows, A->row_ptr, A->col, A->val, x, y, nullptr, (cudaStream_t)stream, A->nnz, 0);
+}
+
+int air_hierarchy_spmv(const air_hierarchy *H, const double *x, double *y, void *stream) {
+    if (!H || !x || !y || x == y) return AIR_ERR_INVALID_ARG;
+    return air_sell_spmv_f64(H->a0, x, y, nullptr, (cudaStream_t)stream);
 }
 
 int air_bicgstab_solve(const air_csr *A, const air_hierarchy *H, const double *b, double *x, double rtol,

@@ -62,6 +62,12 @@ void air_dfree(void *p);
 // all calls: the attribute is per function, and setups running concurrently on
 // several host threads must not lower it under one another's launches.
 #define AIR_SMEM_OPTIN (200 * 1024)
+// Opts kernel f in to AIR_SMEM_OPTIN bytes once per device and process: the
+// attribute is set by the first caller only, so that concurrent setups on
+// several host threads do not keep setting it while instances of the kernel run.
+cudaError_t air_smem_optin_impl(const void *f);
+template <typename F>
+inline cudaError_t air_smem_optin(F *f) { return air_smem_optin_impl((const void *)f); }
 
 // device error flags written by bounded kernels
 #define AIR_DEVERR_RS_CAP 1

@@ -259,7 +259,7 @@ int air_falgout_split(int64_t n, int64_t block, const int64_t *srp, const int32_
     const int64_t ng1 = (block + 31) / 32, ng2 = (block + 1023) / 1024;
     const size_t per_warp = (size_t)(block + ng1 + ng2 + NEWF_CAP) * sizeof(int32_t);
     if (per_warp * FWARPS > AIR_SMEM_OPTIN) return AIR_ERR_UNSUPPORTED;     // block <= 8192 points
-    AIR_CUDA(cudaFuncSetAttribute(local_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, AIR_SMEM_OPTIN));
+    AIR_CUDA(air_smem_optin(local_pass_kernel));
     local_pass_kernel<<<air_counted((unsigned)((nblk + FWARPS - 1) / FWARPS)), FWARPS * 32, per_warp * FWARPS, s>>>(
         n, block, srp, sci, strp, stci, cf, d_err);
     AIR_LAUNCH();

@@ -605,7 +605,7 @@ int air_rs_first_pass_cursor(int64_t n, const int64_t *srp, const int32_t *sci, 
     if (smem > AIR_SMEM_OPTIN) {
         st = AIR_ERR_UNSUPPORTED;
     } else {
-        AIR_CUDA(cudaFuncSetAttribute(rs5_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, AIR_SMEM_OPTIN));
+        AIR_CUDA(air_smem_optin(rs5_warp_kernel));
         rs5_warp_kernel<<<air_counted(1), 32, smem, s>>>(a);
         AIR_LAUNCH();
         rs5_finish_kernel<<<air_counted(blocks_for(n, 256)), 256, 0, s>>>(n, lam, cf);

@@ -904,12 +904,10 @@ int launch_element(const ElemArgs &a, bool gradient, cudaStream_t s) {
     if (smem > AIR_SMEM_OPTIN) return AIR_ERR_UNSUPPORTED;
     const unsigned grid = (unsigned)((a.E + WPB - 1) / WPB);
     if (gradient) {
-        AIR_CUDA(cudaFuncSetAttribute(velocity_gradient_kernel<D, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      AIR_SMEM_OPTIN));
+        AIR_CUDA(air_smem_optin(velocity_gradient_kernel<D, P>));
         velocity_gradient_kernel<D, P><<<air_counted(grid), WPB * 32, smem, s>>>(a);
     } else {
-        AIR_CUDA(cudaFuncSetAttribute(hdg_element_kernel<D, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      AIR_SMEM_OPTIN));
+        AIR_CUDA(air_smem_optin(hdg_element_kernel<D, P>));
         hdg_element_kernel<D, P><<<air_counted(grid), WPB * 32, smem, s>>>(a);
     }
     AIR_LAUNCH();

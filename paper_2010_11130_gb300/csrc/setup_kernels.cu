@@ -1235,7 +1235,7 @@ static int rs_first_pass_v3(int64_t n, const int64_t *srp, const int32_t *sci, c
     AIR_LAUNCH();
     size_t smem = (size_t)a.nb * a.w2 * sizeof(uint64_t) + (size_t)(max_st + 8);
     if (smem > AIR_SMEM_OPTIN) return AIR_ERR_UNSUPPORTED;
-    AIR_CUDA(cudaFuncSetAttribute(rs3_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, AIR_SMEM_OPTIN));
+    AIR_CUDA(air_smem_optin(rs3_warp_kernel));
     rs3_warp_kernel<<<air_counted(1), 32, smem, s>>>(a);
     AIR_LAUNCH();
     rs3_finish_kernel<<<air_counted(grid_for(n, 256)), 256, 0, s>>>(n, lam, cf);
@@ -1290,10 +1290,10 @@ int air_rs_first_pass(int64_t n, const int64_t *srp, const int32_t *sci, const i
     size_t smem = (size_t)a.nb * a.w2 * sizeof(uint64_t) + (size_t)(max_st + 1 + a.touch_cap) * sizeof(int32_t);
     if (smem > AIR_SMEM_OPTIN) return AIR_ERR_UNSUPPORTED;
     if (cached) {
-        AIR_CUDA(cudaFuncSetAttribute(rs_warp_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, AIR_SMEM_OPTIN));
+        AIR_CUDA(air_smem_optin(rs_warp_kernel<true>));
         rs_warp_kernel<true><<<air_counted(1), 32, smem, s>>>(a);
     } else {
-        AIR_CUDA(cudaFuncSetAttribute(rs_warp_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, AIR_SMEM_OPTIN));
+        AIR_CUDA(air_smem_optin(rs_warp_kernel<false>));
         rs_warp_kernel<false><<<air_counted(1), 32, smem, s>>>(a);
     }
     AIR_LAUNCH();
@@ -1339,7 +1339,7 @@ int air_lair_counts(int64_t nc, const int32_t *crows, const int64_t *srp, const 
                     int32_t *cnt, int distance, int *d_err, cudaStream_t s) {
     if (distance >= 2) {
         const size_t smem = (size_t)8 * LAIR_CAP * sizeof(int32_t);
-        AIR_CUDA(cudaFuncSetAttribute(lair_count2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, AIR_SMEM_OPTIN));
+        AIR_CUDA(air_smem_optin(lair_count2_kernel));
         lair_count2_kernel<<<air_counted(grid_for(nc * 32, 256)), 256, smem, s>>>(nc, crows, srp, sci, cf, cnt, d_err);
     } else {
         lair_count_kernel<<<air_counted(grid_for(nc, 256)), 256, 0, s>>>(nc, crows, srp, sci, cf, cnt);
@@ -1384,7 +1384,7 @@ int air_lair_solve(const AirLevel &L, int32_t max_m, int distance, int64_t *d_ns
     int maxm = 0, ld = 0, warps = 0;
     size_t smem = 0;
     AIR_TRY(lair_shape(max_m, distance, &maxm, &ld, &warps, &smem));
-    AIR_CUDA(cudaFuncSetAttribute(lair_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, AIR_SMEM_OPTIN));
+    AIR_CUDA(air_smem_optin(lair_solve_kernel));
     lair_solve_kernel<<<air_counted(lair_blocks(L.nc, warps)), warps * 32, smem, s>>>(lair_job(L, d_nsing, 0), maxm,
                                                                                          ld, distance);
     AIR_LAUNCH();
@@ -1408,8 +1408,7 @@ int air_lair_solve_batch(int count, const AirLevel *const *levels, const int32_t
     LairJob *d_jobs = nullptr;
     AIR_CUDA(cudaMallocAsync(&d_jobs, (size_t)count * sizeof(LairJob), s));
     AIR_CUDA(cudaMemcpyAsync(d_jobs, jobs.data(), (size_t)count * sizeof(LairJob), cudaMemcpyHostToDevice, s));
-    AIR_CUDA(cudaFuncSetAttribute(lair_solve_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  AIR_SMEM_OPTIN));
+    AIR_CUDA(air_smem_optin(lair_solve_batch_kernel));
     lair_solve_batch_kernel<<<air_counted(lair_blocks(total, warps)), warps * 32, smem, s>>>(count, d_jobs, total,
                                                                                                 maxm, ld, distance);
     AIR_LAUNCH();
@@ -1450,8 +1449,7 @@ int rap_launch(const AirLevel &L, int64_t nrows, const int32_t *rows, int bits, 
         if (warps < 1) warps = 1;
         int64_t blocks = (nrows + warps - 1) / warps;
         if (blocks > 152 * 16) blocks = 152 * 16;
-        AIR_CUDA(cudaFuncSetAttribute(rap_kernel<FILL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      AIR_SMEM_OPTIN));
+        AIR_CUDA(air_smem_optin(rap_kernel<FILL, false>));
         rap_kernel<FILL, false><<<air_counted((unsigned)blocks), warps * 32, per_warp * warps, s>>>(
             nrows, rows, L.rrp, L.rci, L.rv, L.rp, L.ci, L.v, L.pcol, bits, nullptr, cnt, acrp, acci, acv);
         AIR_LAUNCH();

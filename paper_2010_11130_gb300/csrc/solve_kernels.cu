@@ -53,7 +53,22 @@ __device__ __forceinline__ A seg_sum(A s) {
 // latency-bound).  Entries beyond U*VL fall to a remainder loop.  The loop
 // runs over blocks of rows with a trip count that is uniform across the
 // warp, so every lane reaches the segment shuffles.
-enum { ROW_SPMV = 0, ROW_JACOBI = 1 };
+// ROW_JACOBI writes a sweep's new values compactly (y[pos], scattered
+// afterwards); ROW_JACOBI_FULL writes them in place of the rows (y[row]) of a
+// second full vector, and the launch's extra blocks copy the rows the sweep
+// leaves unchanged (crows), so that the sweeps alternate between two vectors.
+enum { ROW_SPMV = 0, ROW_JACOBI = 1, ROW_JACOBI_FULL = 2 };
+
+// Block blk of the copy part of a ROW_JACOBI_FULL launch.
+template <typename TX>
+__device__ __forceinline__ void copy_rows(int64_t mc, const int32_t *__restrict__ crows, const TX *__restrict__ x,
+                                          TX *__restrict__ y, int64_t blk) {
+    const int64_t p = blk * blockDim.x + threadIdx.x;
+    if (p < mc) {
+        const int32_t r = crows[p];
+        y[r] = x[r];
+    }
+}
 
 template <typename TV, typename TX>
 struct RowArgs {
@@ -254,6 +269,9 @@ struct SellArgs {
     const TX *dinv;
     const TX *diag;        // FP32 diagonal when the stored values hold none
     TX omega;
+    int64_t mc;            // ROW_JACOBI_FULL: rows copied unchanged from x to y, and the blocks before them
+    const int32_t *crows;
+    int64_t sweep_blocks;
 };
 
 // One thread per row: entry k of the 32 rows of a slice is one coalesced
@@ -261,6 +279,10 @@ struct SellArgs {
 template <int UN, typename TV, typename TX, int MODE>
 __global__ void __launch_bounds__(256) sell_kernel(SellArgs<TV, TX> a) {
     using A = typename Acc<TX>::type;
+    if (MODE == ROW_JACOBI_FULL && (int64_t)blockIdx.x >= a.sweep_blocks) {
+        copy_rows(a.mc, a.crows, a.x, a.y, (int64_t)blockIdx.x - a.sweep_blocks);
+        return;
+    }
     const int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (pos >= a.m) return;
     const int64_t sl = pos >> 5;
@@ -288,7 +310,8 @@ __global__ void __launch_bounds__(256) sell_kernel(SellArgs<TV, TX> a) {
         a.y[row] = a.b ? (TX)((A)a.b[row] - acc) : (TX)acc;
     } else {
         if (a.diag) acc += (A)a.diag[row] * (A)a.x[row];
-        a.y[pos] = (TX)(a.x[row] + a.omega * ((TX)((A)a.b[row] - acc)) * a.dinv[row]);
+        const TX nv = (TX)(a.x[row] + a.omega * ((TX)((A)a.b[row] - acc)) * a.dinv[row]);
+        a.y[MODE == ROW_JACOBI ? pos : row] = nv;
     }
 }
 
@@ -341,6 +364,9 @@ struct BSellArgs {
     const TX *b;
     const TX *dinv;
     TX omega;
+    int64_t mc;            // as in SellArgs
+    const int32_t *crows;
+    int64_t sweep_blocks;
 };
 
 // One thread per row: the row's blocks two at a time, each block's b values
@@ -348,6 +374,10 @@ struct BSellArgs {
 template <int B, bool PAIRS, typename TV, typename TX, int MODE>
 __global__ void __launch_bounds__(256) bsell_kernel(BSellArgs<TV, TX> a) {
     using A = typename Acc<TX>::type;
+    if (MODE == ROW_JACOBI_FULL && (int64_t)blockIdx.x >= a.sweep_blocks) {
+        copy_rows(a.mc, a.crows, a.x, a.y, (int64_t)blockIdx.x - a.sweep_blocks);
+        return;
+    }
     const int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (pos >= a.m) return;
     const int64_t sl = pos >> 5;
@@ -382,13 +412,16 @@ __global__ void __launch_bounds__(256) bsell_kernel(BSellArgs<TV, TX> a) {
     if (MODE == ROW_SPMV) {
         a.y[row] = a.b ? (TX)((A)a.b[row] - acc) : (TX)acc;
     } else {
-        a.y[pos] = (TX)(a.x[row] + a.omega * ((TX)((A)a.b[row] - acc)) * a.dinv[row]);
+        const TX nv = (TX)(a.x[row] + a.omega * ((TX)((A)a.b[row] - acc)) * a.dinv[row]);
+        a.y[MODE == ROW_JACOBI ? pos : row] = nv;
     }
 }
 
 template <int B, typename TV, typename TX, int MODE>
-void bsell_launch_b(const BSellArgs<TV, TX> &a, bool pairs, cudaStream_t s) {
-    const unsigned g = (unsigned)((a.m + 255) / 256);
+void bsell_launch_b(const BSellArgs<TV, TX> &a0, bool pairs, cudaStream_t s) {
+    BSellArgs<TV, TX> a = a0;
+    a.sweep_blocks = (a.m + 255) / 256;
+    const unsigned g = (unsigned)(a.sweep_blocks + (MODE == ROW_JACOBI_FULL ? (a.mc + 255) / 256 : 0));
     if (pairs) bsell_kernel<B, true, TV, TX, MODE><<<air_counted(g), 256, 0, s>>>(a);
     else bsell_kernel<B, false, TV, TX, MODE><<<air_counted(g), 256, 0, s>>>(a);
 }
@@ -414,6 +447,10 @@ void bsell_launch(int b, const BSellArgs<TV, TX> &a, cudaStream_t s) {
 template <int VL, typename TV, typename TX, int MODE>
 __global__ void __launch_bounds__(256) sell_lanes_kernel(SellArgs<TV, TX> a) {
     using A = typename Acc<TX>::type;
+    if (MODE == ROW_JACOBI_FULL && (int64_t)blockIdx.x >= a.sweep_blocks) {   // whole blocks: no lane is left in a shuffle
+        copy_rows(a.mc, a.crows, a.x, a.y, (int64_t)blockIdx.x - a.sweep_blocks);
+        return;
+    }
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t pos = t / VL;
     const int j = (int)(t % VL);
@@ -449,14 +486,20 @@ __global__ void __launch_bounds__(256) sell_lanes_kernel(SellArgs<TV, TX> a) {
         a.y[row] = a.b ? (TX)((A)a.b[row] - acc) : (TX)acc;
     } else {
         if (a.diag) acc += (A)a.diag[row] * (A)a.x[row];
-        a.y[pos] = (TX)(a.x[row] + a.omega * ((TX)((A)a.b[row] - acc)) * a.dinv[row]);
+        const TX nv = (TX)(a.x[row] + a.omega * ((TX)((A)a.b[row] - acc)) * a.dinv[row]);
+        a.y[MODE == ROW_JACOBI ? pos : row] = nv;
     }
 }
 
+// Blocks of the copy part of a ROW_JACOBI_FULL launch.
+inline int64_t copy_blocks(int64_t mc) { return (mc + 255) / 256; }
+
 template <int VL, typename TV, typename TX, int MODE>
-void sell_lanes_launch(const SellArgs<TV, TX> &a, cudaStream_t s) {
-    const unsigned g = (unsigned)((a.m * VL + 255) / 256);
-    sell_lanes_kernel<VL, TV, TX, MODE><<<air_counted(g), 256, 0, s>>>(a);
+void sell_lanes_launch(const SellArgs<TV, TX> &a0, cudaStream_t s) {
+    SellArgs<TV, TX> a = a0;
+    a.sweep_blocks = (a.m * VL + 255) / 256;
+    const int64_t g = a.sweep_blocks + (MODE == ROW_JACOBI_FULL ? copy_blocks(a.mc) : 0);
+    sell_lanes_kernel<VL, TV, TX, MODE><<<air_counted((unsigned)g), 256, 0, s>>>(a);
 }
 
 template <typename TV, typename TX, int MODE>
@@ -470,8 +513,10 @@ void sell_launch(const SellArgs<TV, TX> &a, cudaStream_t s, int lanes = 1) {
     case 32: sell_lanes_launch<32, TV, TX, MODE>(a, s); return;
     default: break;
     }
-    unsigned g = (unsigned)((a.m + 255) / 256);
-    sell_kernel<8, TV, TX, MODE><<<air_counted(g), 256, 0, s>>>(a);
+    SellArgs<TV, TX> b = a;
+    b.sweep_blocks = (a.m + 255) / 256;
+    const int64_t g = b.sweep_blocks + (MODE == ROW_JACOBI_FULL ? copy_blocks(a.mc) : 0);
+    sell_kernel<8, TV, TX, MODE><<<air_counted((unsigned)g), 256, 0, s>>>(b);
 }
 
 __global__ void f2d_kernel(const float *in, double *out, int64_t n) {
@@ -704,6 +749,35 @@ void jacobi_dispatch(const AirLevel &L, const T *diag, const T *dinv, int which,
     if (scatter) scatter_kernel<T><<<air_counted(grid_cap(S.m, 256)), 256, 0, s>>>(S.m, S.rows, tmp, x);
 }
 
+// One Jacobi sweep over the point set `which` from x into the full vector y:
+// the set's rows get their new values, the other set's rows (when copy) their
+// values in x, in the same launch.
+template <typename TV, typename T>
+void jacobi_full_dispatch(const AirLevel &L, const T *diag, const T *dinv, int which, T omega, const T *b,
+                          const T *x, T *y, bool copy, cudaStream_t s) {
+    const Sell &S = L.sset[which], &O = L.sset[1 - which];
+    const int64_t mc = copy ? O.m : 0;
+    if (S.m == 0) {
+        if (mc > 0) {
+            SellArgs<TV, T> a{};
+            a.m = 0; a.x = x; a.y = y; a.mc = mc; a.crows = O.rows; a.sweep_blocks = 0;
+            sell_kernel<8, TV, T, ROW_JACOBI_FULL><<<air_counted((unsigned)copy_blocks(mc)), 256, 0, s>>>(a);
+        }
+        return;
+    }
+    if (S.b > 0) {
+        BSellArgs<TV, T> ba{};
+        ba.m = S.m; ba.ptr = S.ptr; ba.bc = S.bc; ba.v = (const TV *)S.v; ba.dv = (const T *)S.dv; ba.rows = S.rows;
+        ba.x = x; ba.y = y; ba.b = b; ba.dinv = dinv; ba.omega = omega; ba.mc = mc; ba.crows = O.rows;
+        bsell_launch<TV, T, ROW_JACOBI_FULL>(S.b, ba, s);
+        return;
+    }
+    SellArgs<TV, T> a{};
+    a.m = S.m; a.ptr = S.ptr; a.ci = S.ci; a.v = (const TV *)S.v; a.rows = S.rows;
+    a.x = x; a.y = y; a.b = b; a.dinv = dinv; a.diag = diag; a.omega = omega; a.mc = mc; a.crows = O.rows;
+    sell_launch<TV, T, ROW_JACOBI_FULL>(a, s, L.lanes[which]);
+}
+
 // One Jacobi sweep over all points: both point sets from the same old x into
 // the two halves of tmp, then both scatters.
 template <typename TV, typename T>
@@ -760,10 +834,31 @@ int vcycle_t(const air_hierarchy *H, const T *b0, T *x0, cudaStream_t s) {
         T *out = l == 0 ? x0 : (T *)A.x;
         T *alt = (T *)A.x2;
         const T *xc = (const T *)H->lev[l + 1].x;
-        // x = P x_c, then the sweeps in place
-        interp_kernel<T><<<air_counted(grid_cap(A.n, 256)), 256, 0, s>>>(A.n, A.pcol, xc, out);
         const T *diag = (const T *)lvl_diag<TV>(A);
         const T *dinv = lvl_dinv<T>(A);
+        bool gs = false;
+        for (int q = 0; q < ns; ++q) gs = gs || relax[q] >= 'a';
+        if (!gs) {
+            // x = P x_c, then Jacobi sweeps alternating between out and alt,
+            // starting in whichever of the two makes the last sweep end in out
+            T *cur = ns % 2 == 1 ? alt : out, *nxt = ns % 2 == 1 ? out : alt;
+            interp_kernel<T><<<air_counted(grid_cap(A.n, 256)), 256, 0, s>>>(A.n, A.pcol, xc, cur);
+            for (int q = 0; q < ns; ++q) {
+                const char c = relax[q];
+                if (c == 'A') {
+                    jacobi_full_dispatch<TV, T>(A, diag, dinv, 0, omega, bl, cur, nxt, false, s);
+                    jacobi_full_dispatch<TV, T>(A, diag, dinv, 1, omega, bl, cur, nxt, false, s);
+                } else {
+                    jacobi_full_dispatch<TV, T>(A, diag, dinv, c == 'C' ? 1 : 0, omega, bl, cur, nxt, true, s);
+                }
+                T *t = cur;
+                cur = nxt;
+                nxt = t;
+            }
+            continue;
+        }
+        // x = P x_c, then the sweeps in place
+        interp_kernel<T><<<air_counted(grid_cap(A.n, 256)), 256, 0, s>>>(A.n, A.pcol, xc, out);
         for (int q = 0; q < ns; ++q) {
             const char c = relax[q];
             if (c == 'F' || c == 'C') {

@@ -108,3 +108,41 @@ def test_lanes_per_row_rule_and_autotuner(autotune):
     torch.cuda.synchronize()
     xo = O.vcycle(s.rhs)
     assert np.linalg.norm(x.cpu().numpy() - xo) <= 1e-10 * np.linalg.norm(xo)
+
+
+@pytest.mark.parametrize("relax", ["F", "FC", "FCF", "FFCFF", "A", "CAF"])
+@pytest.mark.parametrize("blocked", [False, True])
+def test_alternating_sweeps_match_oracle(relax, blocked):
+    # Jacobi sweeps alternate between two full vectors (each launch also copies
+    # the rows its point set leaves unchanged); odd and even sweep counts end in
+    # the output vector, 'A' sweeps both sets from the same old vector
+    s, b = _system("st2d_n6_p2_nu1e-6")
+    A = air.CSR.from_host(s.row_ptr, s.col, s.val)
+    H = air.setup(A, theta=0.25, max_coarse=100, relax=relax, omega=0.9, block_size=b if blocked else 0)
+    assert H.info(0).block_size == (b if blocked else 0)
+    O = oracle.setup(s.row_ptr, s.col, s.val, theta=0.25, max_coarse=100, relax=relax, omega=0.9)
+    rng = np.random.default_rng(11)
+    for rhs in (s.rhs, rng.standard_normal(s.n)):
+        x = H.vcycle(torch.from_numpy(np.ascontiguousarray(rhs)).cuda())
+        torch.cuda.synchronize()
+        xo = O.vcycle(rhs)
+        assert np.linalg.norm(x.cpu().numpy() - xo) <= 1e-10 * np.linalg.norm(xo)
+
+
+@pytest.mark.parametrize("name", ["st1d_n12_p2", "st2d_n6_p2_nu1e-6"])
+def test_hierarchy_spmv_is_the_operator(name):
+    # air_hierarchy_spmv: the FP64 copy of A that the Krylov solves use (block
+    # form and entry form) against y = A x in float64 on the host
+    s, b = _system(name)
+    A = air.CSR.from_host(s.row_ptr, s.col, s.val)
+    x = np.random.default_rng(5).standard_normal(s.n)
+    rows = np.repeat(np.arange(s.n), np.diff(s.row_ptr))
+    y_ref = np.zeros(s.n)
+    np.add.at(y_ref, rows, s.val * x[s.col])
+    scale = np.zeros(s.n)
+    np.add.at(scale, rows, np.abs(s.val * x[s.col]))
+    for bs in (0, b):
+        H = air.setup(A, theta=0.25, max_coarse=100, block_size=bs)
+        y = H.spmv(torch.from_numpy(x).cuda())
+        torch.cuda.synchronize()
+        assert np.all(np.abs(y.cpu().numpy() - y_ref) <= 1e-14 * scale + 1e-300)
