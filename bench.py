@@ -997,7 +997,9 @@ def run_vcycle(args):
     t = median_time(lambda: H.vcycle(b, x), torch.cuda.current_stream(), args.vcycles, runs=1)
     print(json.dumps({"workload": workload_config(args)["workload"], "vcycle_bytes": vb, "vcycle_s": t,
                       "gbs": vb / t / 1e9, "levels": H.levels(),
-                      "level_sizes": [int(H.info(l).n) for l in range(H.levels())]}), flush=True)
+                      "level_sizes": [int(H.info(l).n) for l in range(H.levels())],
+                      "lanes_per_row": [[H.info(l).lanes_f, H.info(l).lanes_c, H.info(l).lanes_r]
+                                        for l in range(H.levels() - 1)]}), flush=True)
 
 
 def main():

@@ -1131,12 +1131,19 @@ int lanes_rule(const Sell &S) {
     return L;
 }
 
+// Times the candidate lanes per row on the launch the V-cycle makes: a sweep
+// (into the full vector y, with the other point set's rows copied, `other`)
+// or a restriction.
 template <typename TV, typename T>
-int tune_set(const AirLevel &Lv, const Sell &S, bool jacobi, const T *x, const T *b, T *y, const T *dinv,
-             const T *diag, int *out, cudaStream_t s) {
+int tune_set(const AirLevel &Lv, const Sell &S, const Sell *other, bool jacobi, const T *x, const T *b, T *y,
+             const T *dinv, const T *diag, int *out, cudaStream_t s) {
     SellArgs<TV, T> a{};
     a.m = S.m; a.ptr = S.ptr; a.ci = S.ci; a.v = (const TV *)S.v; a.rows = S.rows;
     a.x = x; a.y = y; a.b = b; a.dinv = dinv; a.diag = diag; a.omega = (T)1;
+    if (other) {
+        a.mc = other->m;
+        a.crows = other->rows;
+    }
     const int cand_all[6] = {1, 2, 4, 8, 16, 32};
     const double avg = S.m > 0 ? (double)S.stored / (double)S.m : 0.0;
     cudaEvent_t e0, e1;
@@ -1148,7 +1155,7 @@ int tune_set(const AirLevel &Lv, const Sell &S, bool jacobi, const T *x, const T
         if (c > 1 && (avg / c < 1.0 || (S.m >= 2000000 && c > 2))) continue;
         for (int rep = 0; rep < 4; ++rep) {
             if (rep == 1) cudaEventRecord(e0, s);
-            if (jacobi) sell_launch<TV, T, ROW_JACOBI>(a, s, c);
+            if (jacobi) sell_launch<TV, T, ROW_JACOBI_FULL>(a, s, c);
             else sell_launch<TV, T, ROW_SPMV>(a, s, c);
         }
         cudaEventRecord(e1, s);
@@ -1175,11 +1182,11 @@ int tune_levels(air_hierarchy *H, cudaStream_t s) {
         const T *diag = (const T *)lvl_diag<TV>(L);
         for (int which = 0; which < 2; ++which)
             if (L.sset[which].b == 0 && L.sset[which].m > 0)
-                AIR_TRY((tune_set<TV, T>(L, L.sset[which], true, (const T *)L.x, (const T *)L.b, (T *)L.x2, dinv,
-                                         diag, &L.lanes[which], s)));
+                AIR_TRY((tune_set<TV, T>(L, L.sset[which], &L.sset[1 - which], true, (const T *)L.x, (const T *)L.b,
+                                         (T *)L.x2, dinv, diag, &L.lanes[which], s)));
         if (L.sr.m > 0)
-            AIR_TRY((tune_set<TV, T>(L, L.sr, false, (const T *)L.b, nullptr, (T *)H->lev[q + 1].b, nullptr, nullptr,
-                                     &L.lanes[2], s)));
+            AIR_TRY((tune_set<TV, T>(L, L.sr, nullptr, false, (const T *)L.b, nullptr, (T *)H->lev[q + 1].b, nullptr,
+                                     nullptr, &L.lanes[2], s)));
     }
     return AIR_OK;
 }
