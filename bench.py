@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--no-gpu-assembly", action="store_true")
     ap.add_argument("--no-gs", action="store_true", help="skip the forward Gauss-Seidel variant")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched independent-problems leg")
+    ap.add_argument("--no-nu2", action="store_true", help="skip the nu = 1e-2 half of the workload")
     ap.add_argument("--autotune", type=int, default=1, help="time the lanes per row of every level at setup")
     ap.add_argument("--block-size", type=int, default=-1,
                     help="block form of the finest operator: facet block size b (-1: b of the workload, 0: off)")
@@ -66,9 +67,10 @@ def parse():
     ap.add_argument("--vcycles", type=int, default=100)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="single", choices=["single", "batched", "multirhs", "table2", "largest", "vcycle"],
+    ap.add_argument("--workload", default="single", choices=["single", "batched", "multirhs", "table2", "largest", "vcycle", "adjoint"],
                     help="batched: 16 independent uneven problems set up and solved at once")
     ap.add_argument("--large-n", type=int, default=56, help="largest workload: cubes per direction")
+    ap.add_argument("--adj-n", type=int, default=40, help="adjoint workload: cubes per direction")
     ap.add_argument("--batch-count", type=int, default=16)
     ap.add_argument("--batch-nmin", type=int, default=16)
     ap.add_argument("--batch-nmax", type=int, default=48)
@@ -566,6 +568,33 @@ def run_ours(args):
                    "form": "FP32 hierarchy, FP64 FGMRES; Falgout-style C/F splitting (first pass per block of "
                            "consecutive points, one warp each, then interface rounds)"}
 
+    # the diffusion-significant half of the workload: nu = 1e-2 (GPU-assembled), distance-2 l-AIR,
+    # FP32 hierarchy (one warm-up, one timed step) and FP64 hierarchy (one timed step)
+    nu2 = None
+    if not args.no_nu2 and args.nu != 1e-2:
+        from sthdg.problems import manufactured_2d
+        A2, b2 = gpu_system(manufactured_2d(n=args.n, p=args.p, nu=1e-2))
+
+        def nstep(prec):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            H = air.setup(A2, theta=0.25, distance=2, precision=prec, block_size=block_size(args),
+                          autotune=args.autotune)
+            torch.cuda.synchronize()
+            tsetup = time.perf_counter() - t0
+            t0 = time.perf_counter()
+            x, info = air.gmres_solve(A2, H, b2, rtol=args.rtol)
+            torch.cuda.synchronize()
+            tsolve = time.perf_counter() - t0
+            lv = H.levels()
+            H.free()
+            return {"s": tsetup + tsolve, "setup_s": tsetup, "solve_s": tsolve, "iters": info.iters,
+                    "relres": info.relres, "levels": lv}
+        nstep(1)
+        nu2 = {"f32_precond_fgmres": nstep(1), "f64": nstep(0),
+               "form": "nu = 1e-2, distance-2 l-AIR, FGMRES(30) to the metric's tolerance; wall-clock, data "
+                       "resident; FP32 after one warm-up step"}
+
     # the paper's relaxation: forward Gauss-Seidel on F then all points (level-scheduled), one step
     gs = None
     if not args.no_gs:
@@ -661,7 +690,8 @@ def run_ours(args):
             "solve_stage_s": {k: breakdown[k]["solve_s"] for k in breakdown},
             "falgout_split_f32_precond": falgout,
             "gauss_seidel_fa_f32_precond": gs,
-            "batched_independent_problems": batched},
+            "batched_independent_problems": batched,
+            "nu_1e-2_distance2": nu2},
         "roofline": {"bound": "hbm", "kernel": "V-cycle (FP32 hierarchy, all levels)",
                      "achieved": v32["gbs"], "peak": gbs_peak, "unit": "GB/s",
                      "frac": v32["gbs"] / gbs_peak, "traffic": vcycle_traffic(v32["bytes"]),
@@ -978,6 +1008,101 @@ def run_largest(args):
     print(json.dumps(out), flush=True)
 
 
+def run_adjoint(args):
+    """The adjoint workload: 2D+time on the mapped domain x' = x + 0.05 sin(2 pi t)
+    sin(pi x) sin(pi y) (y likewise) on --adj-n^3 cubes x 6 tetrahedra, p = 2,
+    nu = 1e-4, a piecewise-constant velocity (1, 0.5) + 0.1 N(0, 1) per element
+    (sthdg.problems.mapped_noisy).  One step: GPU assembly, forward l-AIR FGMRES
+    solve (FP32 hierarchy), adjoint solve A^T lambda = u - u_target on the
+    block-scaled transpose with its own hierarchy, the gradient of
+    L = 1/2 ||u - u_target||^2 with respect to the right-hand side (lambda) and
+    to the element velocities (air_hdg_velocity_gradient).  u_target is the trace
+    solution for the noise-free velocity (1, 0.5).  A directional central
+    difference of L (h = 1e-6, along an N(0, 1) velocity direction, solves to
+    1e-12) checks the velocity gradient at full size."""
+    import torch
+    import paper_2010_11130_gb300 as air
+    from paper_2010_11130_gb300 import hdg
+    from sthdg.mesh import build_mesh
+    from sthdg.problems import mapped_noisy
+    air.build()
+    prob = mapped_noisy(args.adj_n, 2, 1e-4)
+    t0 = time.perf_counter()
+    mesh = build_mesh(prob.D, prob.n, reflect=prob.reflect, vertex_map=prob.vertex_map)
+    tab = hdg.HdgTables(3, 2)
+    hm = hdg.HdgMesh.from_mesh(mesh)
+    xv, xf, xF = hdg.points(hm, tab)
+    xv, xf, xF = xv.cpu().numpy(), xf.cpu().numpy(), xF.cpu().numpy()
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+    src, u0, gd = dev(prob.source(xv)), dev(prob.u_initial(xf)), dev(prob.g_dirichlet(xF))
+    gen_s = time.perf_counter() - t0
+    b = tab.b
+    opts = dict(precision=1, block_size=b, autotune=args.autotune)
+
+    def data(ev):
+        evd = dev(ev)
+        vv = evd[:, None, :].expand(xv.shape[0], xv.shape[1], 2).contiguous()
+        vf = evd[:, None, None, :].expand(xf.shape[0], xf.shape[1], xf.shape[2], 2).contiguous()
+        return hdg.HdgData(prob.nu, 10.0 * prob.p ** 2, vv, vf, src, u0, gd)
+
+    def clock(fn):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize()
+        return r, time.perf_counter() - t
+
+    ev0 = prob.elem_velocity.copy()
+    ev_mean = np.broadcast_to(np.array([1.0, 0.5]), ev0.shape).copy()
+    tsys = hdg.assemble(hm, tab, data(ev_mean))
+    Ht = air.setup(tsys.A, **opts)
+    target, _ = air.gmres_solve(tsys.A, Ht, tsys.rhs, rtol=1e-12)
+    del Ht, tsys
+
+    def loss(ev, rtol):
+        sys_ = hdg.assemble(hm, tab, data(ev))
+        H = air.setup(sys_.A, **opts)
+        u, inf = air.gmres_solve(sys_.A, H, sys_.rhs, rtol=rtol)
+        d = u - target
+        return 0.5 * float((d * d).sum())
+
+    def step(rtol):
+        t = {}
+        dat = data(ev0)
+        sys_, t["assemble"] = clock(lambda: hdg.assemble(hm, tab, dat))
+        S, t["forward_setup"] = clock(lambda: air.AdjointSolver(sys_.A, rtol=rtol, block=(b, sys_.diag), **opts))
+        u, t["forward_solve"] = clock(lambda: S.solve(sys_.rhs))
+        g = (u - target).contiguous()
+        _, t["adjoint_transpose_setup"] = clock(lambda: S.adjoint_hierarchy())
+        lam, t["adjoint_solve"] = clock(lambda: S.solve_adjoint(g))
+        gv, t["velocity_gradient"] = clock(lambda: hdg.velocity_gradient(hm, tab, dat, sys_, u, lam))
+        L = 0.5 * float((g * g).sum())
+        return t, L, gv, lam, S.info, S.info_adjoint, sys_.A
+
+    step(args.rtol)                                     # warm-up (module load, pools, graphs)
+    t, L, gv, lam, inf_f, inf_a, A = step(args.rtol)
+    # full-size check of the velocity gradient at tight tolerances
+    _, Lc, gvc, _, _, _, _ = step(1e-12)
+    rng = np.random.default_rng(40)
+    dirn = rng.standard_normal(ev0.shape)
+    h = 1e-6
+    fd = (loss(ev0 + h * dirn, 1e-12) - loss(ev0 - h * dirn, 1e-12)) / (2 * h)
+    ad = float((gvc.cpu().numpy() * dirn).sum())
+    total = sum(t.values())
+    out = {"metric": "adjoint workload: forward + adjoint AIR-FGMRES to 1e-8 and both gradients (s)",
+           "value": total, "unit": "s", "n_gpus": 1, "steps": 1, "warmup": 1, "higher_is_better": False,
+           "dtype": "f32 hierarchy / f64 Krylov", "data": "synthetic",
+           "config": {"workload": f"mapped_noisy_n{args.adj_n}_p2_nu1e-4", "unknowns": int(A.n),
+                      "elements": int(mesh.n_elems), "rtol": args.rtol, "block_size": b},
+           "stages_s": t, "forward_iters": int(inf_f.iters), "adjoint_iters": int(inf_a.iters),
+           "loss": L, "grad_f_norm": float(lam.norm()),
+           "velocity_gradient_check": {"h": h, "direction": "N(0,1) per element component, default_rng(40)",
+                                       "central_difference": fd, "adjoint": ad,
+                                       "rel_diff": abs(fd - ad) / max(abs(fd), 1e-300), "solve_rtol": 1e-12},
+           "generate_s": gen_s}
+    print(json.dumps(out), flush=True)
+
+
 def run_vcycle(args):
     """V-cycles alone on the workload family (the profiling target): FP32
     hierarchy (block form of the finest operator), 3 warm-up V-cycles, then
@@ -1016,6 +1141,8 @@ def main():
         run_largest(args)
     elif args.workload == "vcycle":
         run_vcycle(args)
+    elif args.workload == "adjoint":
+        run_adjoint(args)
     else:
         run_ours(args)
 
