@@ -484,7 +484,7 @@ def run_ours(args):
     clocks.start()
     ms32, inf32, launches32 = timed(1, args.warmup, args.steps)
     clk = clocks.stop()
-    w_o, k_o = max(1, min(args.warmup, 2)), max(1, min(args.steps, 5))
+    w_o, k_o = args.warmup, args.steps
     ms64, inf64, _ = timed(0, w_o, k_o)
     ms16, inf16, _ = timed(2, w_o, k_o)
 
