@@ -1005,6 +1005,31 @@ __global__ void rap_kernel(int64_t nrows, const int32_t *rows, const int64_t *rr
             }
             __syncwarp();
         }
+        if (!FILL) {
+            // COUNT: the number of distinct coarse columns P(j), from a second hash table
+            int32_t *jt = (int32_t *)skey;                  // HS slots (the sort area, unused here)
+            for (int s = lane; s < HS; s += 32) jt[s] = -1;
+            __syncwarp();
+            int heads = 0;
+            for (int s0 = 0; s0 < HS; s0 += 32) {
+                const int32_t j = keys[s0 + lane];
+                const int32_t J = j >= 0 ? pcol[j] : -1;
+                bool fresh = false;
+                if (J >= 0) {
+                    unsigned h = ((unsigned)J * 2654435761u) >> (32 - hs_bits);
+                    while (true) {
+                        const int32_t old = atomicCAS(&jt[h], -1, J);
+                        if (old == -1) { fresh = true; break; }
+                        if (old == J) break;
+                        h = (h + 1) & (HS - 1);
+                    }
+                }
+                heads += __popc(__ballot_sync(FULL, fresh));
+            }
+            if (lane == 0) cnt[t] = heads;
+            __syncwarp();
+            continue;
+        }
         int cntv = 0;
         for (int s0 = 0; s0 < HS; s0 += 32) {
             int s = s0 + lane;
@@ -1430,11 +1455,16 @@ int air_rap_terms(const AirLevel &L, int32_t *terms, cudaStream_t s) {
 }
 
 // Rows whose term count exceeds lim go to the long list, the others to the short one.
-__global__ void rap_split_kernel(int64_t nc, const int32_t *terms, int32_t lim, int32_t *shortr, int32_t *longr,
+// Row classes by table size: class c holds the rows whose table of
+// 2^(min_bits + c) slots is the smallest holding twice their terms (the last
+// class also any longer row).  lists: ncls x nc.
+__global__ void rap_class_kernel(int64_t nc, const int32_t *terms, int min_bits, int ncls, int32_t *lists,
                                  unsigned long long *counts) {
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nc; t += (int64_t)gridDim.x * blockDim.x) {
-        if (terms[t] > lim) longr[atomicAdd(&counts[1], 1ull)] = (int32_t)t;
-        else shortr[atomicAdd(&counts[0], 1ull)] = (int32_t)t;
+        const int64_t want = 2 * (int64_t)(terms[t] > 1 ? terms[t] : 1);
+        int c = 0;
+        while (c < ncls - 1 && ((int64_t)1 << (min_bits + c)) < want) ++c;
+        lists[(int64_t)c * nc + atomicAdd(&counts[c], 1ull)] = (int32_t)t;
     }
 }
 
@@ -1473,28 +1503,32 @@ int air_rap(const AirLevel &L, int64_t *acrp, int32_t *acci, double *acv, int32_
             int32_t max_terms, const int32_t *terms, cudaStream_t s) {
     int bits = 5;
     while ((1 << bits) < 2 * (max_terms > 1 ? max_terms : 1)) ++bits;
-    constexpr int kSmemBits = 12;                 // 4096 slots, 80 KB: the largest shared table
-    if (bits <= kSmemBits) {
-        return fill ? rap_launch<true>(L, L.nc, nullptr, bits, false, nullptr, acrp, acci, acv, s)
-                    : rap_launch<false>(L, L.nc, nullptr, bits, false, cnt, nullptr, nullptr, nullptr, s);
-    }
-    // split the rows: up to 2048 terms in shared memory, longer rows in global scratch
+    constexpr int kSmemBits = 13;                 // 8192 slots, 160 KB: the largest shared table
+    constexpr int kMinBits = 9;                   // 512 slots, 10 KB: 16 warps per SM
+    auto launch = [&](int64_t nrows, const int32_t *rows, int b) {
+        const bool gmem = b > kSmemBits;
+        return fill ? rap_launch<true>(L, nrows, rows, b, gmem, nullptr, acrp, acci, acv, s)
+                    : rap_launch<false>(L, nrows, rows, b, gmem, cnt, nullptr, nullptr, nullptr, s);
+    };
+    if (bits <= kMinBits) return launch(L.nc, nullptr, bits);
+    // rows by class: each class's table the smallest power of two that holds twice its rows'
+    // terms, so short rows get small tables (more warps per SM, less table upkeep); classes
+    // beyond the shared-memory tables use global scratch tables of their own size
+    const int ncls = bits - kMinBits + 1;
+    if (ncls > 24) return AIR_ERR_UNSUPPORTED;
     int32_t *lists = nullptr;
     unsigned long long *counts = nullptr;
-    AIR_CUDA(air_dmalloc((void **)&lists, (size_t)(2 * L.nc + 2) * sizeof(int32_t)));
-    AIR_CUDA(air_dmalloc((void **)&counts, 2 * sizeof(unsigned long long)));
-    AIR_CUDA(cudaMemsetAsync(counts, 0, 2 * sizeof(unsigned long long), s));
-    rap_split_kernel<<<air_counted(grid_for(L.nc, 256)), 256, 0, s>>>(L.nc, terms, 1 << (kSmemBits - 1), lists,
-                                                                      lists + L.nc + 1, counts);
-    unsigned long long hc[2] = {0, 0};
-    AIR_CUDA(cudaMemcpyAsync(hc, counts, sizeof(hc), cudaMemcpyDeviceToHost, s));
+    AIR_CUDA(air_dmalloc((void **)&lists, (size_t)ncls * (size_t)(L.nc > 0 ? L.nc : 1) * sizeof(int32_t)));
+    AIR_CUDA(air_dmalloc((void **)&counts, (size_t)ncls * sizeof(unsigned long long)));
+    AIR_CUDA(cudaMemsetAsync(counts, 0, (size_t)ncls * sizeof(unsigned long long), s));
+    rap_class_kernel<<<air_counted(grid_for(L.nc, 256)), 256, 0, s>>>(L.nc, terms, kMinBits, ncls, lists, counts);
+    AIR_LAUNCH();
+    unsigned long long hc[24] = {};
     AIR_CUDA(cudaStreamSynchronize(s));
-    int st = fill ? rap_launch<true>(L, (int64_t)hc[0], lists, kSmemBits, false, nullptr, acrp, acci, acv, s)
-                  : rap_launch<false>(L, (int64_t)hc[0], lists, kSmemBits, false, cnt, nullptr, nullptr, nullptr, s);
-    if (st == AIR_OK)
-        st = fill ? rap_launch<true>(L, (int64_t)hc[1], lists + L.nc + 1, bits, true, nullptr, acrp, acci, acv, s)
-                  : rap_launch<false>(L, (int64_t)hc[1], lists + L.nc + 1, bits, true, cnt, nullptr, nullptr, nullptr,
-                                      s);
+    AIR_CUDA(cudaMemcpyAsync(hc, counts, (size_t)ncls * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    AIR_CUDA(cudaStreamSynchronize(s));
+    int st = AIR_OK;
+    for (int c = 0; c < ncls && st == AIR_OK; ++c) st = launch((int64_t)hc[c], lists + (int64_t)c * L.nc, kMinBits + c);
     air_dfree(lists);
     air_dfree(counts);
     return st;
