@@ -303,14 +303,15 @@ int air_coarsen_finish(air_hierarchy *H, int l, cudaStream_t s, AirCoarsen *c) {
     int64_t *acrp = nullptr;
     int32_t *acci = nullptr;
     double *acv = nullptr;
-    AIR_TRY(air_rap(L, nullptr, nullptr, nullptr, cnt, 0, max_terms, terms, s));
+    AIR_TRY(air_rap(L, nullptr, nullptr, nullptr, cnt, 0, max_terms, terms, H->d_err, s));
     AIR_TRY(dalloc(&acrp, nc + 1));
     AIR_TRY(air_exclusive_scan_i32(cnt, acrp, nc, s));
     AIR_TRY(read_i64(acrp + nc, &C.nnz, s));
     AIR_TRY(dalloc(&acci, C.nnz));
     AIR_TRY(dalloc(&acv, C.nnz));
-    AIR_TRY(air_rap(L, acrp, acci, acv, nullptr, 1, max_terms, terms, s));
+    AIR_TRY(air_rap(L, acrp, acci, acv, nullptr, 1, max_terms, terms, H->d_err, s));
     dfree(terms);
+    AIR_TRY(check_err(H, s));
     C.rp = acrp;
     C.ci = acci;
     C.v = acv;

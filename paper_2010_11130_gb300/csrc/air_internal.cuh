@@ -290,7 +290,7 @@ int air_onepoint_P(const AirLevel &L, double theta, cudaStream_t s);
 // terms: RAP terms per coarse row (air_rap_terms); rows with more than 2048
 // use a global-memory hash table
 int air_rap(const AirLevel &L, int64_t *acrp, int32_t *acci, double *acv, int32_t *cnt, int fill,
-            int32_t max_terms, const int32_t *terms, cudaStream_t s);
+            int32_t max_terms, const int32_t *terms, int *d_err, cudaStream_t s);
 int air_rap_terms(const AirLevel &L, int32_t *terms, cudaStream_t s);
 int air_coarse_inverse(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, double *inv,
                        double *work, int *d_err, cudaStream_t s);

@@ -975,7 +975,7 @@ template <bool FILL, bool GMEM>
 __global__ void rap_kernel(int64_t nrows, const int32_t *rows, const int64_t *rrp, const int32_t *rci,
                            const double *rv, const int64_t *rp, const int32_t *ci, const double *v,
                            const int32_t *pcol, int hs_bits, unsigned char *gscratch, int32_t *cnt,
-                           const int64_t *acrp, int32_t *acci, double *acv) {
+                           const int64_t *acrp, int32_t *acci, double *acv, int *err) {
     extern __shared__ unsigned char rsm[];
     const int HS = 1 << hs_bits, HH = HS >> 1;
     int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -995,12 +995,14 @@ __global__ void rap_kernel(int64_t nrows, const int32_t *rows, const int64_t *rr
             for (int64_t e = rp[k] + lane; e < rp[k + 1]; e += 32) {
                 int32_t j = ci[e];
                 unsigned h = ((unsigned)j * 2654435761u) >> (32 - hs_bits);
-                while (true) {
+                bool placed = false;
+                for (int probe = 0; probe < HS; ++probe) {      // the table holds twice the row's terms
                     int32_t old = atomicCAS(&keys[h], -1, j);
-                    if (old == -1) { if (FILL) vals[h] = 0.0; break; }
-                    if (old == j) break;
+                    if (old == -1) { if (FILL) vals[h] = 0.0; placed = true; break; }
+                    if (old == j) { placed = true; break; }
                     h = (h + 1) & (HS - 1);
                 }
+                if (!placed) { atomicOr(err, AIR_DEVERR_CAP); continue; }
                 if (FILL) vals[h] = __dadd_rn(vals[h], __dmul_rn(rik, v[e]));
             }
             __syncwarp();
@@ -1017,12 +1019,14 @@ __global__ void rap_kernel(int64_t nrows, const int32_t *rows, const int64_t *rr
                 bool fresh = false;
                 if (J >= 0) {
                     unsigned h = ((unsigned)J * 2654435761u) >> (32 - hs_bits);
-                    while (true) {
+                    bool placed = false;
+                    for (int probe = 0; probe < HS; ++probe) {
                         const int32_t old = atomicCAS(&jt[h], -1, J);
-                        if (old == -1) { fresh = true; break; }
-                        if (old == J) break;
+                        if (old == -1) { fresh = true; placed = true; break; }
+                        if (old == J) { placed = true; break; }
                         h = (h + 1) & (HS - 1);
                     }
+                    if (!placed) atomicOr(err, AIR_DEVERR_CAP);
                 }
                 heads += __popc(__ballot_sync(FULL, fresh));
             }
@@ -1470,7 +1474,7 @@ __global__ void rap_class_kernel(int64_t nc, const int32_t *terms, int min_bits,
 
 template <bool FILL>
 int rap_launch(const AirLevel &L, int64_t nrows, const int32_t *rows, int bits, bool gmem, int32_t *cnt,
-               const int64_t *acrp, int32_t *acci, double *acv, cudaStream_t s) {
+               const int64_t *acrp, int32_t *acci, double *acv, int *err, cudaStream_t s) {
     if (nrows <= 0) return AIR_OK;
     const size_t per_warp = (size_t)(1 << bits) * 20;
     if (!gmem) {
@@ -1481,7 +1485,7 @@ int rap_launch(const AirLevel &L, int64_t nrows, const int32_t *rows, int bits, 
         if (blocks > 152 * 16) blocks = 152 * 16;
         AIR_CUDA(air_smem_optin(rap_kernel<FILL, false>));
         rap_kernel<FILL, false><<<air_counted((unsigned)blocks), warps * 32, per_warp * warps, s>>>(
-            nrows, rows, L.rrp, L.rci, L.rv, L.rp, L.ci, L.v, L.pcol, bits, nullptr, cnt, acrp, acci, acv);
+            nrows, rows, L.rrp, L.rci, L.rv, L.rp, L.ci, L.v, L.pcol, bits, nullptr, cnt, acrp, acci, acv, err);
         AIR_LAUNCH();
         return AIR_OK;
     }
@@ -1492,7 +1496,7 @@ int rap_launch(const AirLevel &L, int64_t nrows, const int32_t *rows, int bits, 
     AIR_CUDA(air_dmalloc((void **)&scratch, per_warp * (size_t)blocks * 8));
     rap_kernel<FILL, true><<<air_counted((unsigned)blocks), 256, 0, s>>>(nrows, rows, L.rrp, L.rci, L.rv, L.rp, L.ci,
                                                                         L.v, L.pcol, bits, scratch, cnt, acrp, acci,
-                                                                        acv);
+                                                                        acv, err);
     cudaError_t e = cudaGetLastError();
     air_dfree(scratch);
     if (e != cudaSuccess) return AIR_ERR_CUDA;
@@ -1500,15 +1504,15 @@ int rap_launch(const AirLevel &L, int64_t nrows, const int32_t *rows, int bits, 
 }
 
 int air_rap(const AirLevel &L, int64_t *acrp, int32_t *acci, double *acv, int32_t *cnt, int fill,
-            int32_t max_terms, const int32_t *terms, cudaStream_t s) {
+            int32_t max_terms, const int32_t *terms, int *d_err, cudaStream_t s) {
     int bits = 5;
     while ((1 << bits) < 2 * (max_terms > 1 ? max_terms : 1)) ++bits;
     constexpr int kSmemBits = 13;                 // 8192 slots, 160 KB: the largest shared table
     constexpr int kMinBits = 9;                   // 512 slots, 10 KB: 16 warps per SM
     auto launch = [&](int64_t nrows, const int32_t *rows, int b) {
         const bool gmem = b > kSmemBits;
-        return fill ? rap_launch<true>(L, nrows, rows, b, gmem, nullptr, acrp, acci, acv, s)
-                    : rap_launch<false>(L, nrows, rows, b, gmem, cnt, nullptr, nullptr, nullptr, s);
+        return fill ? rap_launch<true>(L, nrows, rows, b, gmem, nullptr, acrp, acci, acv, d_err, s)
+                    : rap_launch<false>(L, nrows, rows, b, gmem, cnt, nullptr, nullptr, nullptr, d_err, s);
     };
     if (bits <= kMinBits) return launch(L.nc, nullptr, bits);
     // rows by class: each class's table the smallest power of two that holds twice its rows'
