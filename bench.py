@@ -380,7 +380,7 @@ class FullOracle(threading.Thread):
 
     def __init__(self, s, args):
         super().__init__(daemon=True)
-        self.s, self.args, self.result, self.error = s, args, None, None
+        self.s, self.args, self.result, self.error, self.x = s, args, None, None, None
 
     def run(self):
         try:
@@ -392,8 +392,9 @@ class FullOracle(threading.Thread):
                              copy_levels=False)
             t_setup = time.perf_counter() - t0
             t0 = time.perf_counter()
-            _, its, rr, ok, _ = oracle.gmres(s.row_ptr, s.col, s.val, H, s.rhs, rtol=self.args.rtol)
+            x, its, rr, ok, _ = oracle.gmres(s.row_ptr, s.col, s.val, H, s.rhs, rtol=self.args.rtol)
             t_solve = time.perf_counter() - t0
+            self.x = x
             self.result = {"setup_s": t_setup, "solve_s": t_solve, "iters": its, "relres": rr, "converged": ok,
                            "levels": len(H.sizes())}
         except Exception as e:   # reported in the line, never fatal to the GPU legs
@@ -493,6 +494,7 @@ def run_ours(args):
     rl = {}
     kry = {"s": None, "block_size": 0}
     breakdown = {}
+    sols = {}
     for prec, key in ((1, "f32"), (0, "f64"), (2, "bf16")):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -505,6 +507,7 @@ def run_ours(args):
         _, inf_s = air.gmres_solve(A, H, b, xs, rtol=args.rtol)
         torch.cuda.synchronize()
         t_solve = time.perf_counter() - t0
+        sols[key] = xs.cpu().numpy()
         if key == "f64":
             # the paper's Krylov method on the same hierarchy: BiCGSTAB to the metric's
             # tolerance and to the paper's 1e-12
@@ -672,6 +675,11 @@ def run_ours(args):
         parity_full = {"oracle_iters": cpu["iters"], "gpu_f64_iters": inf64[-1].iters,
                        "gpu_f64_within_one": abs(inf64[-1].iters - cpu["iters"]) <= 1,
                        "gpu_f32_precond_iters": inf32[-1].iters}
+        if full is not None and full.x is not None:
+            # final error of every form against the oracle's FP64 solution (all to the same rtol)
+            xo = full.x
+            no = float(np.linalg.norm(xo))
+            parity_full["final_rel_error_vs_oracle"] = {k: float(np.linalg.norm(v - xo)) / no for k, v in sols.items()}
     if rank != 0:
         return
     v32 = rl["f32"]
