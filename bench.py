@@ -901,7 +901,7 @@ def run_table2(args):
     """The paper's Table 2 study on structured meshes: AIR-preconditioned BiCGSTAB
     iterations to a relative residual of 1e-12 for the rotating Gaussian pulse on its
     time-dependent domain (Section 5.1), over mesh size, p and nu, with the paper's
-    strength pair (coarsening 0.2, R 0.3) and this build's FCF-Jacobi relaxation."""
+    strength pair (coarsening 0.2, R 0.3) and the library's default FCF-Jacobi relaxation."""
     import torch
     import paper_2010_11130_gb300 as air
     from sthdg import assemble

@@ -1,6 +1,6 @@
 """Pins of the oracle's relaxation sweeps (Section 4 solver settings: the paper
 post-relaxes with forward Gauss-Seidel, first on the F points and then on all
-points; this build's default is FCF-Jacobi).
+points; the library's default is FCF-Jacobi).
 
 The V-cycle operator is composed densely from the level matrices by the
 textbook matrix form of each sweep over a point set S:
