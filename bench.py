@@ -174,8 +174,12 @@ def vcycle_bytes(H, wbytes, diag_bytes=0):
     standalone diagonal one per row, in the vector type).  coarsest: x n_L^2 +
     2 x n_L.  BF16 storage (w = 2) keeps FP32 vectors (x = 4) and adds the FP32
     diagonal (diag_bytes per relaxed row).
+    The call takes and returns FP64 vectors: an FP32 or BF16 hierarchy converts
+    b into its finest vector and the result back (8 + 4 and 4 + 8 bytes per
+    finest row), an FP64 one copies them in and out of its finest buffers
+    (16 + 16 bytes per row).
     """
-    total = 0
+    total = 24 * H.info(0).n if wbytes != 8 else 32 * H.info(0).n
     L = H.levels()
     for l in range(L):
         inf = H.info(l)
