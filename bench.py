@@ -427,6 +427,17 @@ def run_reference(args):
 
 
 # -------------------------------------------------------------------- ours
+def max_over_ranks(x, dist, device="cuda"):
+    """The largest of x over all ranks (x itself without a process group): each
+    rank times its own replica, and the job takes as long as the slowest."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_ours(args):
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -475,16 +486,11 @@ def run_ours(args):
         infos = [step(prec) for _ in range(steps)]
         e1.record(stream)
         barrier()
-        ms = e0.elapsed_time(e1)
-        if dist is not None:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(e0.elapsed_time(e1), dist)
         return ms / steps, infos, air.kernel_launches() - k0
 
     # the reported value: FP32 hierarchy inside FP64 FGMRES, W warm-up + K timed
-    # steps; the FP64 and BF16-off-diagonal forms get min(W, 2) warm-up and
-    # min(K, 5) timed steps (the first pass, the same in every form, is most of a step)
+    # steps; the FP64 and BF16-off-diagonal forms the same
     clocks = ClockSampler(local)
     clocks.start()
     ms32, inf32, launches32 = timed(1, args.warmup, args.steps)
