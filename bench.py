@@ -503,6 +503,7 @@ def run_ours(args):
     gbs_peak, peak_kind = peaks()
     rl = {}
     kry = {"s": None, "block_size": 0}
+    lair_roof = None
     breakdown = {}
     sols = {}
     for prec, key in ((1, "f32"), (0, "f64"), (2, "bf16")):
@@ -537,6 +538,13 @@ def run_ours(args):
             H.vcycle(b, xv)
         t = median_time(lambda: H.vcycle(b, xv), stream, args.vcycles)
         if key == "f32":
+            # the local l-AIR solves: LU of an m x m system, (2/3) m^3 + 2 m^2 flops each
+            # (factorisation plus forward and back substitution), m = |N_i| from R's rows
+            lf = 0.0
+            for l in range(H.levels() - 1):
+                m = np.diff(H.export(l, "R.row_ptr")).astype(np.float64) - 1.0
+                lf += float(np.sum(2.0 / 3.0 * m ** 3 + 2.0 * m ** 2))
+            lair_roof = {"flops": lf, "time_s": H.setup_timings()["lair"] / 1e3}
             # the Krylov solves' matrix product: the hierarchy's FP64 copy of A
             yk = torch.empty_like(b)
             for _ in range(3):
@@ -723,6 +731,13 @@ def run_ours(args):
                           "csr_air_spmv": {"kernel": "row_kernel<4,U,double,double,0> (air_spmv: CSR, 4 lanes per row)",
                                            "achieved": sb / t_spmv / 1e9, "frac": sb / t_spmv / 1e9 / gbs_peak,
                                            "algorithmic_bytes": sb, "launch_s": t_spmv}},
+        "roofline_lair": None if lair_roof is None else {
+            "bound": "fp64 alu (nominal)", "kernel": "lair_solve_kernel (one warp per C point, FP64 LU)",
+            "achieved": lair_roof["flops"] / lair_roof["time_s"] / 1e12, "unit": "TFLOP/s", "peak": 1.25,
+            "peak_kind": "nominal FP64 rate (no measured FP64 peak)",
+            "frac": lair_roof["flops"] / lair_roof["time_s"] / 1e12 / 1.25, "flops": lair_roof["flops"],
+            "time_s": lair_roof["time_s"],
+            "note": "the l-AIR phase time includes the neighbourhood gathers; 0.4% of the step"},
         "breakdown": breakdown,
         "bicgstab_f64_hierarchy": bic,
         "dominant_kernel": {
