@@ -142,3 +142,19 @@ def test_solve_batch_mixed_hierarchies_restarts_and_stops():
         assert inf.relres == inf1.relres
         assert torch.equal(x, x1)
     assert float(xs[3].abs().max()) == 0.0
+
+
+def test_solve_batch_with_host_problems():
+    # host CSR, right-hand sides and solutions: staged through the hierarchies'
+    # device buffers, as in the single-problem host path
+    ss = _systems()[:3]
+    As = [air.CSR(np.ascontiguousarray(s.row_ptr, dtype=np.int64), np.ascontiguousarray(s.col, dtype=np.int32),
+                  np.ascontiguousarray(s.val, dtype=np.float64), s.n) for s in ss]
+    Hs = [air.setup(A, theta=0.25, max_coarse=100, precision=1) for A in As]
+    bs = [torch.from_numpy(np.ascontiguousarray(s.rhs)) for s in ss]
+    xs, infos, st = air.gmres_solve_batch(As, Hs, bs, rtol=1e-8)
+    assert st == [0] * len(ss)
+    for A, H, s, x, inf in zip(As, Hs, ss, xs, infos):
+        x1, inf1 = air.gmres_solve(A, H, np.ascontiguousarray(s.rhs), rtol=1e-8)
+        assert inf.iters == inf1.iters and inf.relres == inf1.relres
+        assert np.array_equal(x.numpy(), x1)
